@@ -1,0 +1,76 @@
+/*
+ * hcran_oracle.h -- FP64 CPU oracle of the energy-efficient PD-NOMA H-CRAN
+ * resource allocator (arXiv 1803.07772: Dinkelbach loop of Section III around
+ * the SCALE + Lagrangian dual solve of Section IV-A, Algorithm 1).
+ *
+ * TEST INFRASTRUCTURE.  Only the test suite, the smoke check and the CPU
+ * baseline leg of the benchmark may load this library.  It shares no code,
+ * header or constant with the CUDA solver.
+ */
+#ifndef HCRAN_ORACLE_H
+#define HCRAN_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+  int32_t M, N, K, Ks, l;      /* RRHs (0 = HPN), subcarriers, users, streaming users, NOMA cap */
+  const double *pmax;          /* [M] W   (C3 / C12) */
+  const double *eta;           /* [M]     power-amplifier factor (Sec. II-A power model) */
+  const double *Pc;            /* [M] W   circuit power */
+  const double *Pf;            /* [M] W   fronthaul power */
+  double Bn_hz;                /* subcarrier bandwidth */
+  double N0_w_per_hz;          /* noise PSD; sigma = N0 * Bn */
+  const double *T_s;           /* [Ks] delay targets (C7) */
+  const double *lambda_pps;    /* [Ks] Poisson arrival rates */
+  double zbar_bits;            /* packet size */
+  const double *w;             /* [M*K] priority weights w_{m,k}, NULL = all 1 */
+  const float *G;              /* [N][M][K] channel power gains Gamma (k fastest) */
+} orc_problem;
+
+typedef struct {
+  double tol_dinkelbach;       /* stop when F(q)/R <= tol (Sec. III) */
+  double tol_scale;            /* varpi_2 of Algorithm 1 */
+  double tol_dual;             /* varpi_1 of Algorithm 1 */
+  int32_t max_dinkelbach, max_scale, max_dual;
+  double q_init;               /* > 0: fixed E^1 (else E^1 = R(p^0)/P(p^0)) */
+  double tie_eps;              /* relative margin under which a selection decision counts as a tie */
+} orc_params;
+
+typedef struct {
+  /* caller-allocated arrays (any may be NULL) */
+  int32_t *A;                  /* [K] serving RRH, -1 = unserved */
+  int32_t *S;                  /* [N*M*l] user ids per (n,m) in SIC order, -1 = empty */
+  double *p;                   /* [N*M*l] W */
+  double *alpha, *beta;        /* [N*M*l] SCALE coefficients */
+  double *xi;                  /* [M] */
+  double *zeta;                /* [Ks] */
+  double *zeta_sic;            /* [N*M*l(l-1)/2] */
+  double *q_trace;             /* [max_dinkelbach+1] E^1 = R(p^0)/P(p^0), then E^{i+1} after iteration i */
+  double *F_trace;             /* [max_dinkelbach] F_i = R - q_i P */
+  double *scale_obj_trace;     /* [max_dinkelbach*max_scale] exact R - E^i P after each SCALE pass */
+  int32_t *scale_sel_changed;  /* [max_dinkelbach*max_scale] 1 on the first pass after a selection change */
+  /* scalars written by the oracle */
+  double ee, R, P;
+  int32_t iters[3];            /* Dinkelbach, SCALE (total), dual (total) */
+  int32_t status;              /* bit 0 not converged, bit 1 streaming rate unmet, bit 2 last Dinkelbach pass lowered the EE */
+  double slack_power_min;      /* min_m (pmax - sum p)/pmax */
+  double slack_rate_min;       /* min_k (r_k - Psi_k)/Psi_k over streaming users (exact rate) */
+  double slack_sic_max;        /* max over selected pairs of Omega_bar / mask (<= 0 is feasible) */
+  double min_margin;           /* smallest relative margin of any selection decision */
+  int32_t n_ties;              /* decisions with margin < tie_eps */
+  int32_t n_scale_traced;      /* entries written to the scale traces */
+} orc_result;
+
+int orc_solve(const orc_problem *pr, const orc_params *par, orc_result *out);
+
+/* closed-form pieces, exposed so that tests can pin them on their own */
+double orc_psi(double T_s, double lambda_pps, double zbar_bits, double Bn_hz);   /* C9 */
+void orc_scale_coeffs(double z0, double *alpha, double *beta);                   /* SCALE bound */
+
+#ifdef __cplusplus
+}
+#endif
+#endif

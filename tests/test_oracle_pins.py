@@ -1,0 +1,373 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Every test here checks the oracle against something other than itself: the
+paper's worked example, closed forms (Lambert-W EE optimum, water-filling),
+the quadratic the delay bound comes from, KKT stationarity evaluated by
+finite differences of an independent implementation of the paper's model,
+brute force on micro instances, and the invariants of Lemma 1 / Prop. 1.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from hcran_inputs import Instance, Tolerances, make_workload, WORKLOADS
+from tests import exact_model as em
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LN2 = math.log(2.0)
+SIGMA = 10.0 ** (-17.4) * 1e-3 * 180e3
+
+
+def micro(G, Ks=0, l=1, pmax=None, eta=None, Pc=None, Pf=None, T=0.05, lam=62.5, w=None):
+    """Instance with hand-set gains G[n][m][k] (float32) and the usual constants."""
+    G = np.asarray(G, dtype=np.float32)
+    N, M, K = G.shape
+    return Instance(
+        M=M, N=N, K=K, Ks=Ks, l=l,
+        pmax=np.asarray(pmax if pmax is not None else [1.0] * M, dtype=np.float64),
+        eta=np.asarray(eta if eta is not None else [2.0] * M, dtype=np.float64),
+        Pc=np.asarray(Pc if Pc is not None else [1.0] * M, dtype=np.float64),
+        Pf=np.asarray(Pf if Pf is not None else [1.0] * M, dtype=np.float64),
+        Bn_hz=180e3, N0_w_per_hz=10.0 ** (-17.4) * 1e-3,
+        T_s=np.full(Ks, T), lambda_pps=np.full(Ks, lam), zbar_bits=1024.0, G=G, w=w)
+
+
+TIGHT = Tolerances(tol_dinkelbach=1e-12, tol_scale=1e-11, tol_dual=1e-12,
+                   max_dinkelbach=60, max_scale=400, max_dual=20000)
+
+
+# ---------------------------------------------------------------- delay bound
+
+def test_psi_worked_example():
+    g = json.load(open(os.path.join(HERE, "golden", "psi_worked_example.json")))
+    assert g["T_s"] == pytest.approx(g["queue_packets"] / g["lambda_pps"])
+    v = oracle.psi(g["T_s"], g["lambda_pps"], g["zbar_bits"], g["Bn_hz"])
+    assert abs(v - g["psi_printed_bits_per_s_per_hz"]) < g["printed_digits_tolerance"]
+
+
+@pytest.mark.parametrize("T,lam,z,Bn", [(0.2, 125, 1024, 31250), (0.05, 62.5, 1024, 180e3),
+                                        (0.01, 500, 4096, 15e3), (1.0, 3.0, 512, 1e6)])
+def test_psi_is_smaller_root_of_quadratic(T, lam, z, Bn):
+    """X = zbar/(Psi Bn) is the smaller root of (Eq6b) and meets (3) with equality
+    when the second moment equals the squared mean."""
+    psi = oracle.psi(T, lam, z, Bn)
+    X = z / (psi * Bn)
+    roots = sorted(np.roots([lam, -(2 + 2 * lam * T), 2 * T]).real)
+    assert X == pytest.approx(roots[0], rel=1e-12)
+    assert X + lam * X * X / (2 * (1 - lam * X)) == pytest.approx(T, rel=1e-12)
+    assert roots[0] > 0 and roots[1] > 0
+
+
+# ---------------------------------------------------------------- SCALE bound
+
+@pytest.mark.parametrize("z0", [1e-6, 1e-3, 0.1, 1.0, 3.7, 100.0, 1e5])
+def test_scale_bound_tight_and_below(z0):
+    a, b = oracle.scale_coeffs(z0)
+    assert 0 < a < 1
+    assert a * math.log2(z0) + b == pytest.approx(math.log2(1 + z0), rel=1e-13, abs=1e-15)
+    # tangent at z0 (same slope in log z): a = z0/(1+z0)
+    eps = 1e-6 * z0
+    slope = (math.log1p(z0 + eps) - math.log1p(z0 - eps)) / (2 * eps * LN2)
+    assert a / (z0 * LN2) == pytest.approx(slope, rel=1e-6)
+    z = np.logspace(-8, 8, 10000)
+    assert np.all(a * np.log2(z) + b <= np.log2(1 + z) + 1e-12 * np.maximum(1, np.log2(1 + z)))
+
+
+# ---------------------------------------------------------------- closed forms
+
+def lambert_ee_opt(g, P0, eta, mask):
+    """EE-optimal single-link power: argmax log2(1+g p)/(P0 + eta p)."""
+    from scipy.special import lambertw
+    x = float(lambertw((g * P0 / eta - 1.0) / math.e).real)
+    p = (math.exp(x + 1.0) - 1.0) / g
+    return min(p, mask)
+
+
+@pytest.mark.parametrize("gain,pmax", [(2e-14, 10.0), (5e-15, 0.5), (1e-12, 0.01)])
+def test_single_link_ee_matches_lambert_w(gain, pmax):
+    inst = micro([[[gain]]], pmax=[pmax], eta=[3.0], Pc=[2.0], Pf=[1.0])
+    r = oracle.solve(inst, TIGHT)
+    g = float(np.float32(gain)) / SIGMA     # the instance stores float32 gains
+    p_star = lambert_ee_opt(g, 3.0, 3.0, pmax)
+    ee_star = math.log2(1 + g * p_star) / (3.0 + 3.0 * p_star)
+    assert r.S[0, 0, 0] == 0
+    assert r.p[0, 0, 0] == pytest.approx(p_star, rel=1e-6)
+    assert r.ee == pytest.approx(ee_star, rel=1e-9)
+    # brute-force check of the closed form itself
+    ps = np.linspace(1e-9, pmax, 200001)
+    assert ee_star >= np.max(np.log2(1 + g * ps) / (3.0 + 3.0 * ps)) * (1 - 1e-9)
+
+
+def test_oma_single_rrh_is_waterfilling_at_fixed_E():
+    """One RRH, OMA (l = 1), elastic users, fixed E: every subcarrier goes to the
+    user with the larger water-filling utility and gets p = [1/(ln2 E eta) - 1/g]."""
+    rng = np.random.default_rng(7)
+    N, K = 6, 3
+    G = (10.0 ** rng.uniform(-14.5, -13.0, size=(N, 1, K))).astype(np.float32)
+    E, eta, pmax = 2.0, 4.0, 5.0
+    inst = micro(G, pmax=[pmax], eta=[eta])
+    r = oracle.solve(inst, TIGHT, q_init=E, max_dinkelbach=1)
+    mask = pmax / N
+    level = 1.0 / (LN2 * E * eta)
+    for n in range(N):
+        g = G[n, 0, :].astype(np.float64) / SIGMA
+        pk = np.clip(level - 1.0 / g, 0.0, mask)
+        u = np.log2(1 + g * pk) - E * eta * pk
+        k_best = int(np.argmax(u))
+        assert r.S[n, 0, 0] == k_best
+        assert r.p[n, 0, 0] == pytest.approx(pk[k_best], rel=1e-7)
+    assert np.all(r.xi == 0)
+
+
+# ---------------------------------------------------------------- KKT by finite differences
+
+def lagrangian(inst, P, r, E):
+    """L of problem (final_Problem_formulation_1) with exact rates, using the
+    oracle's multipliers: elastic rate - E * power + rate and budget and SIC terms."""
+    sigma = inst.N0_w_per_hz * inst.Bn_hz
+    Ke = inst.K - inst.Ks
+    rk = em.rates(inst.G, P, sigma, inst.w)
+    L = rk[:Ke].sum() - E * (inst.eta[None, :, None] * P[:, :, :Ke]).sum()
+    if inst.Ks:
+        L += np.dot(r.zeta, rk[Ke:] - em.psi(inst))
+    L -= np.dot(r.xi, P.sum(axis=(0, 2)) - inst.pmax)
+    l = inst.l
+    for n in range(inst.N):
+        for m in range(inst.M):
+            idx = 0
+            for a in range(l):
+                for b in range(a + 1, l):
+                    ka, kb = r.S[n, m, a], r.S[n, m, b]
+                    if ka >= 0 and kb >= 0 and r.zeta_sic[n, m, idx] > 0:
+                        L -= r.zeta_sic[n, m, idx] * em.omega_bar(inst, P, n, m, ka, kb)
+                    idx += 1
+    return L
+
+
+def check_stationary(inst, r, E, rtol=2e-5):
+    P = em.dense_power(r.S, r.p, inst.K)
+    mask = inst.pmax / inst.N
+    checked = 0
+    for (n, m, s), k in np.ndenumerate(r.S):
+        if k < 0:
+            continue
+        p = r.p[n, m, s]
+        if not (1e-6 * mask[m] < p < mask[m] * (1 - 1e-9)):
+            continue
+        h = 1e-5
+        Pp, Pm = P.copy(), P.copy()
+        Pp[n, m, k] = p * math.exp(h)
+        Pm[n, m, k] = p * math.exp(-h)
+        dL = (lagrangian(inst, Pp, r, E) - lagrangian(inst, Pm, r, E)) / (2 * h)
+        c = 1.0 if k < inst.K - inst.Ks else r.zeta[k - (inst.K - inst.Ks)]
+        scale = c / LN2
+        assert abs(dL) <= rtol * scale, (n, m, s, k, dL, scale)
+        checked += 1
+    return checked
+
+
+def test_kkt_two_interfering_links():
+    """Two RRHs, one user each, asymmetric cross gains: the fixed point of
+    eq. (653) is a stationary point of the exact Lagrangian (catches a
+    transposed interference gain or a wrong price sign)."""
+    G = [[[1e-12, 4e-14], [9e-14, 2e-12]]]   # G[n][m][k]
+    inst = micro(G, pmax=[1.0, 1.0], eta=[2.0, 3.0])
+    E = 1.0
+    r = oracle.solve(inst, TIGHT, q_init=E, max_dinkelbach=1)
+    assert list(r.A) == [0, 1]
+    assert check_stationary(inst, r, E) == 2
+
+
+def test_kkt_noma_pair_same_rrh():
+    """One RRH, two NOMA users on one subcarrier: the weak user hears the
+    strong one, not the reverse (Sec. II-A SIC order)."""
+    G = [[[1e-12, 4e-14]]]
+    inst = micro(G, l=2, pmax=[1.0], eta=[2.0])
+    E = 0.2
+    r = oracle.solve(inst, TIGHT, q_init=E, max_dinkelbach=1)
+    assert list(r.S[0, 0]) == [0, 1]
+    assert check_stationary(inst, r, E) == 2
+    P = em.dense_power(r.S, r.p, 2)
+    g = em.sinr(inst.G, P, SIGMA)
+    assert g[0, 0, 0] == pytest.approx(r.p[0, 0, 0] * 1e-12 / SIGMA, rel=1e-6)
+
+
+def test_kkt_with_streaming_user():
+    """A streaming user whose rate constraint binds: stationarity with the
+    oracle's zeta', and the exact rate meets Psi."""
+    rng = np.random.default_rng(3)
+    G = (10.0 ** rng.uniform(-14.0, -12.5, size=(3, 2, 3))).astype(np.float32)
+    G[:, 0, 2] *= 0.02   # streaming user far from RRH 0
+    inst = micro(G, Ks=1, l=2, pmax=[2.0, 1.0], eta=[4.0, 2.0], T=0.01, lam=400.0)
+    E = 0.5
+    r = oracle.solve(inst, TIGHT, q_init=E, max_dinkelbach=1)
+    assert r.A[2] >= 0 and r.zeta[0] > 0
+    # the elastic links sit at the mask here; the two interior links are the
+    # streaming user's, whose price carries zeta'
+    assert check_stationary(inst, r, E, rtol=1e-4) >= 2
+    P = em.dense_power(r.S, r.p, inst.K)
+    rk = em.rates(inst.G, P, SIGMA)
+    assert rk[2] >= em.psi(inst)[0] * (1 - 1e-5)
+
+
+# ---------------------------------------------------------------- exact R, P, EE
+
+@pytest.mark.parametrize("name", ["small-3x8x6"])
+def test_reported_R_P_match_independent_model(name):
+    inst = make_workload(name)[0]
+    r = oracle.solve(inst, WORKLOADS[name]["tol"])
+    P = em.dense_power(r.S, r.p, inst.K)
+    R, Pt = em.R_P(inst, P)
+    assert r.R == pytest.approx(R, rel=1e-12)
+    assert r.P == pytest.approx(Pt, rel=1e-12)
+    assert r.ee == pytest.approx(R / Pt, rel=1e-12)
+    assert r.q_trace[-1] == pytest.approx(R / Pt, rel=1e-12)
+
+
+# ---------------------------------------------------------------- invariants
+
+def structural_checks(inst, r):
+    N, M, l = r.S.shape
+    mask = inst.pmax / inst.N
+    for n in range(N):
+        for m in range(M):
+            ids = [k for k in r.S[n, m] if k >= 0]
+            assert all(k >= 0 for k in r.S[n, m, :len(ids)])          # packed
+            assert len(set(ids)) == len(ids) <= l                     # C1
+            for k in ids:
+                assert r.A[k] == m                                    # C5
+            g = [float(inst.G[n, m, k]) for k in ids]
+            assert all(g[i] > g[i + 1] or (g[i] == g[i + 1] and ids[i] < ids[i + 1])
+                       for i in range(len(ids) - 1))                  # SIC order
+            for s, k in enumerate(r.S[n, m]):
+                if k >= 0:
+                    assert mask[m] * 1e-9 * (1 - 1e-12) <= r.p[n, m, s] <= mask[m] * (1 + 1e-12)  # C4
+    P = em.dense_power(r.S, r.p, inst.K)
+    assert np.all(P.sum(axis=(0, 2)) <= inst.pmax * (1 + 1e-12))     # C12 after projection
+
+
+@pytest.mark.parametrize("name", ["small-3x8x6", "medium-9x64x48"])
+def test_dinkelbach_and_constraints(name):
+    inst = make_workload(name)[0]
+    r = oracle.solve(inst, WORKLOADS[name]["tol"])
+    structural_checks(inst, r)
+    q, F = r.q_trace, r.F_trace
+    # Prop. 1: F_i = P(p^i)(E^{i+1} - E^i) > 0 and E increases until the stop test fires
+    assert len(F) == len(q) - 1 >= 1
+    for i in range(len(F) - 1):
+        assert F[i] > 0 and q[i + 1] > q[i]
+    last_ok = F[-1] <= WORKLOADS[name]["tol"].tol_dinkelbach * (q[-1] * r.P) + 1e-9
+    assert last_ok or r.iters[0] == WORKLOADS[name]["tol"].max_dinkelbach
+    if inst.Ks:
+        assert r.slack_rate_min > -1e-3 or (r.status & 2)
+    assert r.slack_sic_max < 1e-2
+
+
+def test_scale_objective_nondecreasing_fixed_selection():
+    """Prop. 2: with the selection fixed and the bound tight at the start of a
+    pass (s >= 1), the exact objective R - E P does not decrease."""
+    rng = np.random.default_rng(11)
+    G = (10.0 ** rng.uniform(-14.0, -12.5, size=(4, 2, 4))).astype(np.float32)
+    inst = micro(G, l=2, pmax=[2.0, 1.0], eta=[4.0, 2.0])
+    r = oracle.solve(inst, TIGHT, q_init=0.8, max_dinkelbach=1)
+    tr = r.scale_obj_trace
+    assert len(tr) >= 3
+    d = np.diff(tr[1:])
+    assert np.all(d >= -1e-9 * np.abs(tr[1:-1]).max())
+
+
+# ---------------------------------------------------------------- brute force on micro instances
+
+def _ee_of(inst, P):
+    R, Pt = em.R_P(inst, P)
+    return R / Pt
+
+
+def brute_force_ee(inst, starts=6, sweeps=12, seed=0):
+    """Best EE over every assignment (A, S) obeying C1/C5, with powers found by
+    coordinate golden-section search from several starts; points violating
+    C12 or C14 are discarded.  A lower bound on the global optimum."""
+    import itertools
+    rng = np.random.default_rng(seed)
+    N, M, K, l = inst.N, inst.M, inst.K, inst.l
+    mask = inst.pmax / N
+    best = 0.0
+
+    def feasible(P):
+        if np.any(P.sum(axis=(0, 2)) > inst.pmax * (1 + 1e-12)):
+            return False
+        for n in range(N):
+            for m in range(M):
+                ids = [k for k in range(K) if P[n, m, k] > 0]
+                ids.sort(key=lambda k: (-float(inst.G[n, m, k]), k))
+                for a in range(len(ids)):
+                    for b in range(a + 1, len(ids)):
+                        if em.omega_bar(inst, P, n, m, ids[a], ids[b]) > 0:
+                            return False
+        return True
+
+    def value(P):
+        return _ee_of(inst, P) if feasible(P) else -1.0
+
+    for A in itertools.product(range(-1, M), repeat=K):
+        # every per-(m,n) subset of the users of m with size <= l
+        per = []
+        for n in range(N):
+            for m in range(M):
+                users = [k for k in range(K) if A[k] == m]
+                subs = [c for r_ in range(0, min(l, len(users)) + 1)
+                        for c in itertools.combinations(users, r_)]
+                per.append((n, m, subs))
+        for choice in itertools.product(*[s for _, _, s in per]):
+            links = [(n, m, k) for (n, m, _), sub in zip(per, choice) for k in sub]
+            if not links:
+                continue
+            served = {k for _, _, k in links}
+            if any(A[k] >= 0 and k not in served for k in range(K)):
+                continue   # an RRH assignment without links is the same as A_k = -1
+            for st in range(starts):
+                P = np.zeros((N, M, K))
+                for (n, m, k) in links:
+                    P[n, m, k] = mask[m] * rng.uniform(0.05, 1.0)
+                if not feasible(P):
+                    continue
+                cur = value(P)
+                for _ in range(sweeps):
+                    for (n, m, k) in links:
+                        lo, hi = mask[m] * 1e-6, mask[m]
+                        gr = (math.sqrt(5) - 1) / 2
+                        for _it in range(40):
+                            a_ = hi - gr * (hi - lo)
+                            b_ = lo + gr * (hi - lo)
+                            Pa, Pb = P.copy(), P.copy()
+                            Pa[n, m, k], Pb[n, m, k] = a_, b_
+                            if value(Pa) >= value(Pb):
+                                hi = b_
+                            else:
+                                lo = a_
+                        Pn = P.copy()
+                        Pn[n, m, k] = 0.5 * (lo + hi)
+                        vn = value(Pn)
+                        if vn > cur:
+                            P, cur = Pn, vn
+                best = max(best, cur)
+    return best
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("shape,seed", [((1, 2, 3), 5), ((2, 1, 3), 6)])
+def test_oracle_not_above_brute_force(shape, seed):
+    """Brute force stands in for the paper's monotonic-optimisation optimum:
+    the oracle (a local method) cannot beat it and stays close to it."""
+    N, M, K = shape
+    rng = np.random.default_rng(seed)
+    G = (10.0 ** rng.uniform(-14.0, -12.5, size=(N, M, K))).astype(np.float32)
+    inst = micro(G, l=2, pmax=[1.0] * M, eta=[2.0] * M)
+    r = oracle.solve(inst, Tolerances())
+    bf = brute_force_ee(inst)
+    assert r.ee <= bf * (1 + 1e-3)
+    assert r.ee >= 0.5 * bf
