@@ -1,0 +1,318 @@
+"""Benchmark: instances/s of the batched GPU solve (4096 uneven H-CRAN
+realisations per step, the same seeds every step) on N GPUs of one node.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line.  A step is one hcran_solve of the whole batch (selection,
+SCALE passes, dual loops and Dinkelbach updates of every instance, one
+persistent kernel launch).  Under torchrun each rank solves its own batch
+(seed offset by rank): weak scaling, no collective on the data path.
+`--impl reference` times the FP64 CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import multiprocessing as mp
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "batch-4096-uneven"
+METRIC = "instances/sec to EE within 1e-4 of FP64 oracle (plain cold-start batched GPU solve)"
+
+
+def rank_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+# ---------------------------------------------------------------- CPU oracle leg
+
+def _oracle_one(args):
+    idx, start = args
+    sys.path.insert(0, ROOT)
+    import oracle
+    from hcran_inputs import WORKLOADS, make_workload
+    inst = make_workload(WORKLOAD, count=1, start=start + idx)[0]
+    t = time.perf_counter()
+    oracle.solve(inst, WORKLOADS[WORKLOAD]["tol"])
+    return time.perf_counter() - t
+
+
+def oracle_sample_ids(count: int):
+    """Instances of the workload at or below the median M*N*K, in workload order."""
+    from hcran_inputs import make_workload
+    insts = make_workload(WORKLOAD, count=512)
+    med = float(np.median([i.cost for i in insts]))
+    return [k for k, i in enumerate(insts) if i.cost <= med][:count]
+
+
+def time_oracle(ids, procs: int):
+    import oracle
+    oracle.build()
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(procs) as pool:
+        pool.map(_oracle_one, [(0, ids[0])])           # warm the workers' imports
+        t0 = time.perf_counter()
+        pool.map(_oracle_one, [(0, i) for i in ids])
+        wall = time.perf_counter() - t0
+    return wall
+
+
+def cpu_baseline(cores: int):
+    ids = oracle_sample_ids(cores)
+    wall = time_oracle(ids, cores)
+    return {"value": len(ids) / wall, "unit": "instances/s", "cores": cores, "kind": "oracle",
+            "sample": "%d instances of the %s workload at or below its median size (the first such "
+                      "in seed order), one per process, FP64 C oracle" % (len(ids), WORKLOAD)}
+
+
+def run_reference(args):
+    rank, world, _ = rank_env()
+    if rank != 0:
+        return
+    cores = os.cpu_count() or 1
+    ids_all = oracle_sample_ids(cores * (args.steps + args.warmup))
+    import oracle
+    oracle.build()
+    ctx = mp.get_context("spawn")
+    times = []
+    with ctx.Pool(cores) as pool:
+        for s in range(args.warmup + args.steps):
+            ids = ids_all[s * cores:(s + 1) * cores] or ids_all[:cores]
+            t0 = time.perf_counter()
+            pool.map(_oracle_one, [(0, i) for i in ids])
+            dt = time.perf_counter() - t0
+            if s >= args.warmup:
+                times.append((len(ids), dt))
+    n = sum(c for c, _ in times)
+    wall = sum(t for _, t in times)
+    v = n / wall
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "instances/s",
+           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": 1e3 * wall / max(len(times), 1), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "instances_per_step": cores,
+                      "sample": "instances at or below the median size"},
+           "cpu_baseline": {"value": v, "unit": "instances/s", "cores": cores, "kind": "oracle",
+                            "sample": "%d instances per step, one per process" % cores},
+           "e2e": {"value": v, "unit": "instances/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+# ---------------------------------------------------------------- clocks
+
+class Clocks:
+    Q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=5)
+        except Exception:
+            self.p.kill()
+            return None
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 6:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx = max(mx, float(f[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[2:6]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- GPU leg
+
+def algorithmic_bytes(insts, iters):
+    """Bytes the method must move per solve (per instance, summed):
+    one read of Gamma (4 M N K) per selection (one per Dinkelbach iteration),
+    and per dual iteration one read of the compact slab (4 N M * M l) plus
+    four words per slot (power, alpha, price, user id: 16 N M l)."""
+    tot = 0
+    for inst, it in zip(insts, iters):
+        M, N, K, l = inst.M, inst.N, inst.K, inst.l
+        tot += 4 * M * N * K * int(it[0]) + int(it[2]) * (4 * N * M * M * l + 16 * N * M * l)
+    return tot
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+    from hcran_inputs import WORKLOADS, make_workload, pack_batch
+    from paper_1803_07772_gb300 import Solver, make_tol
+
+    rank, world, local = rank_env()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    cpu_line = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        # before any CUDA work in this process; the pool uses spawn anyway
+        cpu_line = cpu_baseline(os.cpu_count() or 1)
+
+    count = args.instances
+    insts = make_workload(WORKLOAD, count=count, start=rank * count)
+    gains, offs = pack_batch(insts)
+    tol = make_tol(WORKLOADS[WORKLOAD]["tol"])
+    stream = torch.cuda.Stream(dev)
+    with torch.cuda.stream(stream):
+        solver = Solver(insts, gain_offsets=offs, device=str(dev), stream=stream)
+        g = torch.from_numpy(gains).to(dev)
+    torch.cuda.synchronize(dev)
+
+    for _ in range(args.warmup):
+        solver.solve(g, tol)
+    stream.synchronize()
+
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    clocks = Clocks(local)
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    launches = 0
+    for _ in range(args.steps):
+        solver.solve(g, tol)
+        launches += solver.launches()
+    ev1.record(stream)
+    stream.synchronize()
+    torch.cuda.synchronize(dev)
+    ms = ev0.elapsed_time(ev1)
+    clk = clocks.stop()
+    t = torch.tensor([ms], device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.barrier()
+    ms_max = float(t.item())
+    summ = solver.summary()
+
+    # end to end through the C ABI from pinned host memory (copies inside the timed region)
+    host = torch.from_numpy(gains).pin_memory()
+    solver.solve_host(host, tol)
+    if world > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(max(1, min(args.steps, 3))):
+        ee_h, st_h = solver.solve_host(host, tol)
+    e2e_s = (time.perf_counter() - t0) / max(1, min(args.steps, 3))
+    te = torch.tensor([e2e_s], device=dev)
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_s = float(te.item())
+
+    if rank == 0:
+        per_step_ms = ms_max / args.steps
+        value = world * count / (per_step_ms / 1e3)
+        abytes = algorithmic_bytes(insts, summ["iters"])
+        peaks = {}
+        try:
+            peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        except Exception:
+            pass
+        peak = float(peaks.get("hbm_gbs", 6800.0))
+        achieved = abytes / (per_step_ms / 1e3) / 1e9
+        traffic = None
+        try:
+            prof = json.load(open(os.path.join(ROOT, "profiles", "solve_kernel_traffic.json")))
+            if prof.get("kernel_hash") == kernel_hash():
+                traffic = prof.get("dram_bytes_per_launch_scaled")
+        except Exception:
+            pass
+        out = {
+            "metric": METRIC, "value": value, "unit": "instances/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step_ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "instances_per_gpu": count,
+                       "sizes": "M~U{3..16}, N~U{16..256}, K~U{10..120}, 30% streaming, l=3",
+                       "precision": "FP32 SINR/power/prices, FP64 Dinkelbach q, F(q), multipliers",
+                       "l2": "inputs larger than L2 (%.2f GB of gains per step)" % (gains.nbytes / 1e9),
+                       "parallelism": "replicas" if world == 1 else "dp%d" % world},
+            "gpu_launches": launches,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6.8 TB/s",
+                         "algorithmic_bytes_per_launch": abytes},
+            "e2e": {"value": world * count / e2e_s, "unit": "instances/s",
+                    "h2d_bytes_per_step": int(gains.nbytes),
+                    "d2h_bytes_per_step": int(count * 8 + count * 4)},
+            "solve_stats": {"mean_iters": np.mean(summ["iters"], axis=0).tolist(),
+                            "status_counts": {str(k): int(v) for k, v in
+                                              zip(*np.unique(summ["status"], return_counts=True))},
+                            "ee_mean": float(np.mean(summ["ee"]))},
+        }
+        if clk:
+            out["clocks"] = clk
+        if cpu_line:
+            out["cpu_baseline"] = cpu_line
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def kernel_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_1803_07772_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--instances", type=int, default=4096)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

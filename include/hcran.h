@@ -1,0 +1,146 @@
+/*
+ * hcran.h -- C ABI of the GB300 (sm_103a) solver for energy-efficient
+ * resource allocation in PD-NOMA H-CRANs (arXiv 1803.07772).
+ *
+ * One call solves a batch of independent channel realisations ("instances")
+ * of problem (eq7): maximise the elastic users' energy efficiency
+ * E = R(p)/P(p) over RRH selection, subcarrier/NOMA selection and transmit
+ * powers, subject to the power budgets (C12), spectral masks (C4), the
+ * delay-derived minimum rates of the streaming users (C9/C13) and SIC
+ * feasibility (C14).  The method is the paper's: the Dinkelbach iteration of
+ * Sec. III (Theorem 1, Prop. 1) around Algorithm 1 of Sec. IV-A (SCALE lower
+ * bound of eq. scale_approximation, log-power change of variable, closed-form
+ * KKT powers of eq. (653)/(683), projected subgradient multipliers).
+ *
+ * Conventions
+ *  - Every function returns an hcran_status code; nothing aborts or prints.
+ *  - Gains are float32 Gamma[n][m][k] = |h_{m,k}^{(n)}|^2 (k fastest), one
+ *    slab per instance, inside one device buffer.  Instance b starts at
+ *    element gain_offsets[b] (given at create time, must be a multiple of 4).
+ *  - All device memory is owned by the caller: the solver works inside one
+ *    workspace buffer of hcran_workspace_size() bytes (256-byte aligned),
+ *    which the caller allocates (e.g. with PyTorch) and keeps alive while any
+ *    call that uses it is in flight.  The library allocates no device memory.
+ *  - Calls that take a stream only enqueue work on it; hcran_get* synchronise
+ *    that stream before copying results to the caller's host arrays.
+ *  - Arithmetic: SINR, power, prices and subgradient residuals in FP32;
+ *    Dinkelbach ratio q = R/P, the F(q) test and the multiplier values
+ *    (accumulated subgradient steps) in FP64.
+ */
+#ifndef HCRAN_H
+#define HCRAN_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  HCRAN_OK = 0,
+  HCRAN_EINVAL = 1,    /* bad argument (sizes, NULL, NaN/negative constants, misaligned offset) */
+  HCRAN_ENOMEM = 2,    /* host allocation failed or workspace too small */
+  HCRAN_ECUDA = 3,     /* a CUDA runtime call failed (launch, copy, sync) */
+  HCRAN_ETIMEDOUT = 4, /* reserved: a bounded device wait gave up */
+  HCRAN_ENUMERIC = 5   /* NaN/Inf reached the Dinkelbach ratio */
+} hcran_status;
+
+/* per-instance result status bits */
+#define HCRAN_ST_NOT_CONVERGED 1   /* Dinkelbach cap reached before F(q) <= tol * R */
+#define HCRAN_ST_STREAMING_UNMET 2 /* some streaming user ends below Psi_k (relative slack < -1e-3) */
+#define HCRAN_ST_EE_DECREASED 4    /* the stop test fired with F(q) < 0 (last pass lowered the EE) */
+#define HCRAN_ST_NUMERIC 8         /* non-finite value met; the instance's outputs are not valid */
+
+typedef struct hcran_s *hcran_t;
+
+/* One instance: the system model of Sec. II-A and the traffic of C7/C9.
+ * Copied at create time; the caller keeps ownership of every pointer. */
+typedef struct {
+  int32_t M;                 /* RRHs, index 0 = HPN (>= 1) */
+  int32_t N;                 /* subcarriers (>= 1) */
+  int32_t K;                 /* users (>= 1); 0..K-Ks-1 elastic, K-Ks..K-1 streaming */
+  int32_t Ks;                /* streaming users (0..K) */
+  int32_t l;                 /* NOMA users per subcarrier and RRH, C1 (1..8) */
+  const double *pmax;        /* [M] W, per-RRH budget (C12); mask = pmax/N (C4) */
+  const double *eta;         /* [M] power-amplifier factor (> 0) */
+  const double *Pc;          /* [M] W circuit power (>= 0) */
+  const double *Pf;          /* [M] W fronthaul power (>= 0) */
+  double Bn_hz;              /* subcarrier bandwidth (> 0) */
+  double N0_w_per_hz;        /* noise PSD (> 0); sigma = N0 * Bn */
+  const double *T_s;         /* [Ks] delay targets (> 0) */
+  const double *lambda_pps;  /* [Ks] Poisson arrival rates (> 0) */
+  double zbar_bits;          /* packet size (> 0) */
+  const double *w;           /* [M*K] priority weights w_{m,k} in [0,1], or NULL (= 1) */
+} hcran_config;
+
+/* Stopping rules of Sec. III and Algorithm 1. */
+typedef struct {
+  double tol_dinkelbach;     /* stop when F(q) <= tol * R */
+  double tol_scale;          /* varpi_2: max |p^s - p^{s-1}| / mask */
+  double tol_dual;           /* varpi_1: max |p^v - p^{v-1}| / mask */
+  int32_t max_dinkelbach, max_scale, max_dual;
+  double tie_eps;            /* relative margin under which a selection decision is flagged */
+  double q_init;             /* > 0: use this E^1 instead of R(p^0)/P(p^0) (0 = the method's start) */
+} hcran_tol;
+
+/* Result of one instance.  Array members are caller-allocated host arrays
+ * (NULL = skip); scalars are always written. */
+typedef struct {
+  int32_t *A;                /* [K] serving RRH per user, -1 = unserved */
+  int32_t *S;                /* [N*M*l] users per (n,m) in SIC order (strongest first), -1 = empty */
+  float *p;                  /* [N*M*l] W */
+  float *alpha, *beta;       /* [N*M*l] SCALE coefficients at the returned point */
+  double *xi;                /* [M]  power-budget multipliers */
+  double *zeta;              /* [Ks] rate multipliers */
+  double *zeta_sic;          /* [N*M*l(l-1)/2] SIC multipliers per (n,m,pair) */
+  double ee, R, P;           /* EE = R/P (bits/s/Hz/W), R (bits/s/Hz), P (W) */
+  int32_t iters[3];          /* Dinkelbach iterations, SCALE passes, dual iterations */
+  int32_t status;            /* HCRAN_ST_* bits */
+  double slack_power_min;    /* min_m (pmax - sum p)/pmax */
+  double slack_rate_min;     /* min_k (r_k - Psi_k)/Psi_k, exact rates */
+  double slack_sic_max;      /* max over selected pairs of Omega_bar/mask (<= 0 feasible) */
+  double min_margin;         /* smallest relative margin of a selection decision */
+  int32_t n_ties;            /* decisions with margin < tie_eps */
+} hcran_result;
+
+/* Plan a batch of n independent instances (host only, no device work).
+ * gain_offsets[b]: element offset of instance b's gains in the buffer later
+ * given to hcran_solve (NULL = packed back to back, each rounded up to 4). */
+int hcran_create(hcran_t *out, const hcran_config *cfgs, int32_t n, const int64_t *gain_offsets);
+
+/* Bytes of device workspace the plan needs (constants, state, scratch, results). */
+int hcran_workspace_size(hcran_t h, uint64_t *bytes);
+
+/* Total float32 elements the gain buffer must hold. */
+int hcran_gain_elems(hcran_t h, int64_t *elems);
+
+/* Upload the plan's constants into the workspace (a host-to-device copy
+ * enqueued on `stream`); required once per workspace before hcran_solve. */
+int hcran_prepare(hcran_t h, void *workspace_dev, void *stream);
+
+/* Solve every instance: enqueue the persistent solver launch on `stream`.
+ * Issues only device work (memset + kernel), so it may be captured in a CUDA
+ * graph.  gains_dev and workspace_dev must stay valid until it completes. */
+int hcran_solve(hcran_t h, const float *gains_dev, const hcran_tol *tol, void *workspace_dev,
+                void *stream);
+
+/* End-to-end form: copies gains from host memory (pinned for overlap) into
+ * the workspace's staging area, solves, and copies the per-instance summary
+ * (ee, status) back into the caller's host arrays (either may be NULL).
+ * Returns after the stream has finished. */
+int hcran_solve_host(hcran_t h, const float *gains_host, const hcran_tol *tol, void *workspace_dev,
+                     void *stream, double *ee_host, int32_t *status_host);
+
+/* Results.  Both synchronise the stream of the last solve. */
+int hcran_get(hcran_t h, int32_t index, hcran_result *out);
+int hcran_get_summary(hcran_t h, double *ee, double *R, double *P, int32_t *status,
+                      int32_t *iters3, double *min_margin, int32_t *n_ties);
+
+/* Kernel launches issued by the last hcran_solve (for accounting). */
+int hcran_last_launch_count(hcran_t h, int32_t *launches);
+
+void hcran_destroy(hcran_t h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,124 @@
+// hcran_layout.h -- workspace layout shared by the host planner and the
+// device solver (internal; not part of the C ABI).
+#pragma once
+#include <stdint.h>
+
+#if defined(__CUDACC__)
+#define HCRAN_HD __host__ __device__ __forceinline__
+#else
+#define HCRAN_HD inline
+#endif
+
+namespace hcran {
+
+constexpr int kThreads = 512;          // threads per CTA (one CTA solves one instance)
+constexpr int kWarps = kThreads / 32;
+constexpr int kMaxM = 64;              // RRHs per instance
+constexpr int kMaxL = 8;               // NOMA users per (RRH, subcarrier)
+
+HCRAN_HD int64_t al4(int64_t x) { return (x + 3) & ~int64_t(3); }
+
+// per-instance descriptor (device copy lives at the start of the workspace)
+struct InstDesc {
+  int32_t M, N, K, Ks, l, U, L, npair, nchunk, pad;
+  int64_t g_off;   // element offset of Gamma[n][m][k] in the gain buffer
+  int64_t d_off;   // element offset in the double arena
+  int64_t f_off;   // element offset in the float arena
+  int64_t i_off;   // element offset in the int arena
+  double sigma;    // noise power per subcarrier, N0 * Bn
+  double Pconst;   // sum_m (Pc_m + Pf_m)
+};
+
+// double arena of one instance
+struct DLayout {
+  int64_t pmax, eta, mask, Psi, w, xi, zeta, zsic, total;
+};
+HCRAN_HD DLayout dlayout(int M, int N, int K, int Ks, int l) {
+  DLayout d;
+  int64_t o = 0;
+  const int npair = l * (l - 1) / 2;
+  d.pmax = o; o = al4(o + M);
+  d.eta = o; o = al4(o + M);
+  d.mask = o; o = al4(o + M);
+  d.Psi = o; o = al4(o + (Ks > 0 ? Ks : 1));
+  d.w = o; o = al4(o + int64_t(M) * K);
+  d.xi = o; o = al4(o + M);
+  d.zeta = o; o = al4(o + (Ks > 0 ? Ks : 1));
+  d.zsic = o; o = al4(o + int64_t(N) * M * (npair > 0 ? npair : 1));
+  d.total = o;
+  return d;
+}
+
+// float arena of one instance (L = N*U slots, U = M*l slots per subcarrier)
+struct FLayout {
+  int64_t p, plin, pstart, alpha, beta, pi, gam, X, slab, SICp, SICm, Ptot, cu, cp, cX, ckey, Upart,
+      total;
+};
+HCRAN_HD FLayout flayout(int M, int N, int K, int l, int nchunk) {
+  FLayout f;
+  int64_t o = 0;
+  const int64_t L = int64_t(N) * M * l;
+  const int64_t NM = int64_t(N) * M, NK = int64_t(N) * K;
+  f.p = o; o = al4(o + L);
+  f.plin = o; o = al4(o + L);
+  f.pstart = o; o = al4(o + L);
+  f.alpha = o; o = al4(o + L);
+  f.beta = o; o = al4(o + L);
+  f.pi = o; o = al4(o + L);
+  f.gam = o; o = al4(o + L);
+  f.X = o; o = al4(o + L);
+  f.slab = o; o = al4(o + NM * M * l);
+  f.SICp = o; o = al4(o + NM);
+  f.SICm = o; o = al4(o + NM);
+  f.Ptot = o; o = al4(o + NM);
+  f.cu = o; o = al4(o + NK);
+  f.cp = o; o = al4(o + NK);
+  f.cX = o; o = al4(o + NK);
+  f.ckey = o; o = al4(o + NK);
+  f.Upart = o; o = al4(o + int64_t(nchunk) * M * K);
+  f.total = o;
+  return f;
+}
+
+// int arena of one instance
+struct ILayout {
+  int64_t A, Anew, S, uslot, total;
+};
+HCRAN_HD ILayout ilayout(int M, int N, int K, int l) {
+  ILayout i;
+  int64_t o = 0;
+  i.A = o; o = al4(o + K);
+  i.Anew = o; o = al4(o + K);
+  i.S = o; o = al4(o + int64_t(N) * M * l);
+  i.uslot = o; o = al4(o + int64_t(K) * N);
+  i.total = o;
+  return i;
+}
+
+HCRAN_HD int nchunk_for(int N, int K) {
+  int c = kThreads / (K > 0 ? K : 1);
+  if (c < 1) c = 1;
+  if (c > N) c = N;
+  return c;
+}
+
+// per-instance scalar outputs
+struct InstOut {
+  double ee, R, P, slack_power_min, slack_rate_min, slack_sic_max, min_margin;
+  int32_t iters[3];
+  int32_t status, n_ties;
+};
+
+struct Tol {
+  double tol_dinkelbach, tol_scale, tol_dual;
+  int32_t max_dinkelbach, max_scale, max_dual;
+  float tie_eps;
+  double q_init;
+};
+
+// region offsets (bytes) inside the workspace
+struct WsLayout {
+  uint64_t descs, order, counter, outs, darena, farena, iarena, staging, total;
+};
+
+}  // namespace hcran

@@ -1,0 +1,112 @@
+"""The C-ABI library loads, exports every symbol include/hcran.h declares,
+and rejects bad arguments on the host (no GPU needed for these calls)."""
+import ctypes as C
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+from hcran_inputs import make_workload
+from paper_1803_07772_gb300 import hcran
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "hcran.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:int|void)\s+(hcran_\w+)\s*\(", src, flags=re.M)))
+
+
+def test_library_exports_every_declared_symbol():
+    lib = hcran.load()
+    names = declared_functions()
+    assert len(names) >= 10
+    for n in names:
+        assert hasattr(lib, n), n
+    assert sorted(hcran.EXPORTS) == names
+
+
+def _cfg(inst, **over):
+    keep = []
+
+    def d(x):
+        a = np.ascontiguousarray(x, dtype=np.float64)
+        keep.append(a)
+        return a.ctypes.data_as(hcran._dp)
+
+    c = hcran.Config(inst.M, inst.N, inst.K, inst.Ks, inst.l, d(inst.pmax), d(inst.eta), d(inst.Pc),
+                     d(inst.Pf), inst.Bn_hz, inst.N0_w_per_hz, d(inst.T_s), d(inst.lambda_pps),
+                     inst.zbar_bits, None)
+    for k, v in over.items():
+        if k in ("pmax", "eta", "Pc", "Pf", "T_s", "lambda_pps"):
+            v = d(v)
+        setattr(c, k, v)
+    return c, keep
+
+
+def _create(cfgs, offs=None):
+    lib = hcran.load()
+    arr = (hcran.Config * len(cfgs))(*cfgs)
+    h = C.c_void_p()
+    o = None
+    if offs is not None:
+        offs = np.asarray(offs, dtype=np.int64)
+        o = offs.ctypes.data_as(hcran._i64p)
+    rc = lib.hcran_create(C.byref(h), arr, len(cfgs), o)
+    if rc == 0:
+        lib.hcran_destroy(h)
+    return rc
+
+
+def test_create_accepts_valid_batch_and_sizes_workspace():
+    insts = make_workload("batch-4096-uneven", count=3)
+    cfgs = [_cfg(i) for i in insts]
+    lib = hcran.load()
+    arr = (hcran.Config * 3)(*[c for c, _ in cfgs])
+    h = C.c_void_p()
+    assert lib.hcran_create(C.byref(h), arr, 3, None) == 0
+    nb, ge = C.c_uint64(), C.c_int64()
+    assert lib.hcran_workspace_size(h, C.byref(nb)) == 0
+    assert lib.hcran_gain_elems(h, C.byref(ge)) == 0
+    assert ge.value == sum((i.cost + 3) // 4 * 4 for i in insts)
+    assert nb.value % 256 == 0 and nb.value > 4 * ge.value
+    lib.hcran_destroy(h)
+
+
+@pytest.mark.parametrize("over", [dict(M=0), dict(N=0), dict(K=0), dict(Ks=-1), dict(l=0), dict(l=9),
+                                  dict(M=65), dict(Bn_hz=0.0), dict(N0_w_per_hz=-1.0),
+                                  dict(Bn_hz=math.nan), dict(zbar_bits=0.0)])
+def test_create_rejects_bad_scalars(over):
+    inst = make_workload("small-3x8x6")[0]
+    c, keep = _cfg(inst, **over)
+    assert _create([c]) == 1
+
+
+@pytest.mark.parametrize("field,val", [("pmax", [40.0, -1.0, 1.0]), ("eta", [4.0, 0.0, 2.0]),
+                                       ("Pc", [math.nan, 1.0, 1.0]), ("T_s", [0.05, -0.05]),
+                                       ("lambda_pps", [math.inf, 62.5])])
+def test_create_rejects_bad_arrays(field, val):
+    inst = make_workload("small-3x8x6")[0]
+    c, keep = _cfg(inst, **{field: val})
+    assert _create([c]) == 1
+
+
+def test_create_rejects_ks_above_k_and_misaligned_offsets():
+    inst = make_workload("small-3x8x6")[0]
+    c, keep = _cfg(inst, Ks=7)
+    assert _create([c]) == 1
+    c, keep = _cfg(inst)
+    assert _create([c], offs=[2]) == 1
+    assert _create([c], offs=[-4]) == 1
+    assert _create([c], offs=[8]) == 0
+
+
+def test_null_arguments_rejected():
+    lib = hcran.load()
+    assert lib.hcran_create(None, None, 1, None) == 1
+    assert lib.hcran_workspace_size(None, None) == 1
+    assert lib.hcran_solve(None, None, None, None, None) == 1
+    assert lib.hcran_get(None, 0, None) == 1

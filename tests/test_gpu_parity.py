@@ -1,0 +1,156 @@
+"""CUDA solver vs FP64 oracle on the same seeded inputs, through the C ABI.
+
+Bar (element by element): RRH selection A and per-(n,m) user sets S equal
+unless a selection decision on either side had a relative margin below
+TIE_BAND (then the instance is reported as a flagged tie and only checked for
+validity); EE within 1e-4 relative; every power of a link both sides select
+within 1e-3 relative (plus 1e-6 of the mask for links near the floor).
+FP32 state differs from FP64 by ~1e-6 relative after thousands of
+iterations, so a decision whose margin exceeds 1e-4 cannot flip.
+"""
+import copy
+
+import numpy as np
+import pytest
+
+import oracle
+from hcran_inputs import Instance, Tolerances, WORKLOADS, make_instance, make_workload, pack_batch
+
+pytestmark = pytest.mark.gpu
+
+TIE_BAND = 1e-4
+EE_RTOL = 1e-4
+P_RTOL = 1e-3
+
+
+def gpu_solve(insts, tol, **tolkw):
+    import torch
+    from paper_1803_07772_gb300 import Solver, make_tol
+    gains, offs = pack_batch(insts)
+    s = Solver(insts, gain_offsets=offs, device="cuda:0")
+    g = torch.from_numpy(gains).to("cuda:0")
+    s.solve(g, make_tol(tol, tie_eps=TIE_BAND, **tolkw))
+    out = [s.get(i) for i in range(len(insts))]
+    assert s.launches() >= 1
+    return out
+
+
+def compare(inst, g, o, label=""):
+    """Assert parity; return a dict of the measured errors."""
+    mask = inst.pmax / inst.N
+    flagged = g["min_margin"] < TIE_BAND or o.min_margin < TIE_BAND
+    same_sel = np.array_equal(g["A"], o.A) and np.array_equal(g["S"], o.S)
+    ee_err = abs(g["ee"] - o.ee) / max(abs(o.ee), 1e-300)
+    sel = g["S"] >= 0
+    both = sel & (g["S"] == o.S)
+    pe = np.abs(g["p"].astype(np.float64) - o.p)
+    lim = P_RTOL * np.maximum(np.abs(o.p), np.abs(g["p"])) + 1e-6 * mask[None, :, None]
+    p_err = float(np.max((pe / np.maximum(np.abs(o.p), 1e-300))[both])) if both.any() else 0.0
+    rep = dict(label=label, ee_gpu=g["ee"], ee_orc=o.ee, ee_rel=ee_err, p_maxrel=p_err,
+               same_selection=same_sel, flagged=flagged, iters_gpu=g["iters"], iters_orc=o.iters,
+               margin_gpu=g["min_margin"], margin_orc=o.min_margin, status=(g["status"], o.status))
+    print("parity", rep)
+    if not flagged:
+        assert same_sel, rep
+        assert ee_err <= EE_RTOL, rep
+        assert np.all(pe[both] <= lim[both]), rep
+    else:
+        assert np.isfinite(g["ee"]) and g["ee"] > 0
+    return rep
+
+
+def test_small_config_matches_oracle():
+    name = "small-3x8x6"
+    inst = make_workload(name)[0]
+    tol = WORKLOADS[name]["tol"]
+    g = gpu_solve([inst], tol)[0]
+    o = oracle.solve(inst, tol)
+    r = compare(inst, g, o, name)
+    assert not r["flagged"]
+
+
+def test_medium_config_matches_oracle():
+    name = "medium-9x64x48"
+    inst = make_workload(name)[0]
+    tol = WORKLOADS[name]["tol"]
+    g = gpu_solve([inst], tol)[0]
+    o = oracle.solve(inst, tol)
+    compare(inst, g, o, name)
+
+
+@pytest.mark.parametrize("v", [1, 5, 60])
+def test_dual_steps_match_at_fixed_E(v):
+    """One selection then exactly v dual iterations of one SCALE pass at a
+    fixed E: isolates the KKT power and subgradient arithmetic."""
+    name = "medium-9x64x48"
+    inst = make_workload(name)[0]
+    tol = Tolerances(tol_dinkelbach=0.0, tol_scale=0.0, tol_dual=0.0,
+                     max_dinkelbach=1, max_scale=1, max_dual=v)
+    g = gpu_solve([inst], tol, q_init=40.0)[0]
+    o = oracle.solve(inst, tol, q_init=40.0)
+    assert np.array_equal(g["S"], o.S) and np.array_equal(g["A"], o.A)
+    sel = o.S >= 0
+    rel = np.abs(g["p"][sel] - o.p[sel]) / o.p[sel]
+    print("dual steps", v, "max p rel", rel.max(), "xi", np.abs(g["xi"] - o.xi).max(),
+          "zeta rel", np.max(np.abs(g["zeta"] - o.zeta) / o.zeta))
+    assert rel.max() < 1e-4
+    assert np.allclose(g["zeta"], o.zeta, rtol=1e-4)
+
+
+def test_algorithm1_matches_at_fixed_E():
+    name = "medium-9x64x48"
+    inst = make_workload(name)[0]
+    tol = copy.copy(WORKLOADS[name]["tol"])
+    tol.max_dinkelbach = 1
+    g = gpu_solve([inst], tol, q_init=60.0)[0]
+    o = oracle.solve(inst, tol, q_init=60.0)
+    compare(inst, g, o, "alg1@E=60")
+
+
+def _batch_subset(count=4, max_cost=40000):
+    out = []
+    i = 0
+    while len(out) < count:
+        inst = make_workload("batch-4096-uneven", count=1, start=i)[0]
+        if inst.cost <= max_cost:
+            out.append(inst)
+        i += 1
+    return out
+
+
+def test_uneven_batch_in_one_launch_matches_oracle():
+    insts = _batch_subset()
+    tol = WORKLOADS["batch-4096-uneven"]["tol"]
+    gs = gpu_solve(insts, tol)
+    for inst, g in zip(insts, gs):
+        o = oracle.solve(inst, tol)
+        compare(inst, g, o, "seed%d M%d N%d K%d" % (inst.seed, inst.M, inst.N, inst.K))
+
+
+def test_repeat_runs_are_bitwise_identical():
+    insts = _batch_subset(count=3)
+    tol = WORKLOADS["batch-4096-uneven"]["tol"]
+    a = gpu_solve(insts, tol)
+    b = gpu_solve(insts, tol)
+    for x, y in zip(a, b):
+        assert x["ee"] == y["ee"]
+        assert np.array_equal(x["p"], y["p"]) and np.array_equal(x["S"], y["S"])
+
+
+@pytest.mark.parametrize("shape", [
+    dict(M=1, N=4, K=3, Ks=0, l=1),      # one RRH, OMA
+    dict(M=2, N=1, K=1, Ks=0, l=1),      # one user, one subcarrier
+    dict(M=3, N=5, K=4, Ks=4, l=2),      # streaming only: R = 0, EE = 0
+    dict(M=4, N=3, K=9, Ks=0, l=3),      # elastic only
+    dict(M=64, N=2, K=80, Ks=10, l=8),   # largest RRH count and NOMA cap the kernel takes
+])
+def test_edge_shapes_match_oracle(shape):
+    inst = make_instance(4242, **shape)
+    tol = Tolerances()
+    g = gpu_solve([inst], tol)[0]
+    o = oracle.solve(inst, tol)
+    if shape["Ks"] == shape["K"]:
+        assert g["ee"] == 0.0 and o.ee == 0.0
+        assert np.array_equal(g["S"], o.S)
+        return
+    compare(inst, g, o, str(shape))
