@@ -49,17 +49,18 @@ typedef enum {
 #define HCRAN_ST_STREAMING_UNMET 2 /* some streaming user ends below Psi_k (relative slack < -1e-3) */
 #define HCRAN_ST_EE_DECREASED 4    /* the stop test fired with F(q) < 0 (last pass lowered the EE) */
 #define HCRAN_ST_NUMERIC 8         /* non-finite value met; the instance's outputs are not valid */
+#define HCRAN_ST_TIMEOUT 16        /* a bounded wait for a shared-memory copy gave up; outputs not valid */
 
 typedef struct hcran_s *hcran_t;
 
 /* One instance: the system model of Sec. II-A and the traffic of C7/C9.
  * Copied at create time; the caller keeps ownership of every pointer. */
 typedef struct {
-  int32_t M;                 /* RRHs, index 0 = HPN (>= 1) */
+  int32_t M;                 /* RRHs, index 0 = HPN (1..64) */
   int32_t N;                 /* subcarriers (>= 1) */
   int32_t K;                 /* users (>= 1); 0..K-Ks-1 elastic, K-Ks..K-1 streaming */
   int32_t Ks;                /* streaming users (0..K) */
-  int32_t l;                 /* NOMA users per subcarrier and RRH, C1 (1..8) */
+  int32_t l;                 /* NOMA users per subcarrier and RRH, C1 (1..8); M*l <= 256 */
   const double *pmax;        /* [M] W, per-RRH budget (C12); mask = pmax/N (C4) */
   const double *eta;         /* [M] power-amplifier factor (> 0) */
   const double *Pc;          /* [M] W circuit power (>= 0) */
@@ -103,6 +104,12 @@ typedef struct {
 } hcran_result;
 
 /* Plan a batch of n independent instances (host only, no device work).
+ * Returns HCRAN_EINVAL for a bad config, or when the largest instance's
+ * per-warp shared working buffers (about 4 * (5 M l + 7 M + M l(l-1)/2 + 2 Ks)
+ * bytes per warp, 16 warps) exceed 220 KB.  When the per-warp double staging
+ * buffers of one subcarrier's state (about 8 * (M*l*(M + 8) + M l(l-1)) bytes
+ * per warp) also fit, the dual loop streams that state through shared memory
+ * with bulk copies; otherwise it reads it from global memory.
  * gain_offsets[b]: element offset of instance b's gains in the buffer later
  * given to hcran_solve (NULL = packed back to back, each rounded up to 4). */
 int hcran_create(hcran_t *out, const hcran_config *cfgs, int32_t n, const int64_t *gain_offsets);
@@ -134,6 +141,13 @@ int hcran_solve_host(hcran_t h, const float *gains_host, const hcran_tol *tol, v
 int hcran_get(hcran_t h, int32_t index, hcran_result *out);
 int hcran_get_summary(hcran_t h, double *ee, double *R, double *P, int32_t *status,
                       int32_t *iters3, double *min_margin, int32_t *n_ties);
+
+/* Per-instance SM clock cycles spent in each phase of the last solve
+ * (cycles[8*b + i]: 0 selection, 1 interference/SINR/prices, 2 multiplier
+ * steps, 3 KKT power update, 4 SCALE coefficient update, 5 projection and
+ * Dinkelbach update, 6 whole instance, 7 reserved), read by the CTA's first
+ * thread with clock64().  Synchronises the stream of the last solve. */
+int hcran_get_phase_cycles(hcran_t h, int64_t *cycles);
 
 /* Kernel launches issued by the last hcran_solve (for accounting). */
 int hcran_last_launch_count(hcran_t h, int32_t *launches);

@@ -17,7 +17,7 @@
 namespace hcran {
 cudaError_t launch_solve(const InstDesc *descs, const int *order, int n_inst, const float *gains,
                          double *darena, float *farena, int *iarena, InstOut *outs, const Tol &tol,
-                         int *counter, cudaStream_t stream, int *launches);
+                         const KDims &kd, int *counter, cudaStream_t stream, int *launches);
 }
 
 using namespace hcran;
@@ -29,6 +29,7 @@ struct hcran_s {
   std::vector<double> dimage;   // full double arena (constants + zeroed multipliers)
   int64_t gain_elems = 0, dtot = 0, ftot = 0, itot = 0;
   WsLayout ws{};
+  KDims kd{0, 0, 0, 0, 0, 0};
   void *last_ws = nullptr;
   cudaStream_t last_stream = nullptr;
   int32_t last_launches = 0;
@@ -50,7 +51,7 @@ static double min_rate(double T, double lam, double zbar, double Bn) {
 
 static int check_config(const hcran_config &c) {
   if (c.M < 1 || c.M > kMaxM || c.N < 1 || c.K < 1 || c.Ks < 0 || c.Ks > c.K || c.l < 1 ||
-      c.l > kMaxL)
+      c.l > kMaxL || c.M * c.l > kMaxU)
     return HCRAN_EINVAL;
   if (int64_t(c.N) * c.M * c.K > (int64_t(1) << 40)) return HCRAN_EINVAL;
   if (!c.pmax || !c.eta || !c.Pc || !c.Pf) return HCRAN_EINVAL;
@@ -112,7 +113,16 @@ extern "C" int hcran_create(hcran_t *out, const hcran_config *cfgs, int32_t n,
       d.d_off = doff; doff += al4(dl.total);
       d.f_off = foff; foff += al4(fl.total);
       d.i_off = ioff; ioff += al4(il.total);
+      h->kd.Upmax = std::max(h->kd.Upmax, slot_stride(c.M, c.l));
+      h->kd.Mmax = std::max(h->kd.Mmax, d.M);
+      h->kd.NPmax = std::max(h->kd.NPmax, d.npair);
+      h->kd.NPPmax = std::max(h->kd.NPPmax, pair_stride(c.M, c.l));
+      h->kd.KSmax = std::max(h->kd.KSmax, d.Ks);
     }
+    // stage per-subcarrier state in shared memory when the double buffers fit
+    h->kd.staged = 1;
+    if (dyn_smem_bytes(h->kd) > kMaxDynSmem) h->kd.staged = 0;
+    if (dyn_smem_bytes(h->kd) > kMaxDynSmem) { delete h; return HCRAN_EINVAL; }
     h->gain_elems = al4(h->gain_elems);
     h->dtot = doff; h->ftot = foff; h->itot = ioff;
     // constants image of the double arena
@@ -209,7 +219,7 @@ static int do_solve(hcran_t h, const float *gains_dev, const hcran_tol *tol, voi
       reinterpret_cast<const InstDesc *>(ws + h->ws.descs), reinterpret_cast<const int *>(ws + h->ws.order),
       h->n, gains_dev, reinterpret_cast<double *>(ws + h->ws.darena),
       reinterpret_cast<float *>(ws + h->ws.farena), reinterpret_cast<int *>(ws + h->ws.iarena),
-      reinterpret_cast<InstOut *>(ws + h->ws.outs), t, reinterpret_cast<int *>(ws + h->ws.counter),
+      reinterpret_cast<InstOut *>(ws + h->ws.outs), t, h->kd, reinterpret_cast<int *>(ws + h->ws.counter),
       static_cast<cudaStream_t>(stream), &launches);
   h->last_ws = workspace_dev;
   h->last_stream = static_cast<cudaStream_t>(stream);
@@ -262,6 +272,14 @@ static bool copy_out(T *dst, const char *src, size_t count) {
   return cudaMemcpy(dst, src, sizeof(T) * count, cudaMemcpyDeviceToHost) == cudaSuccess;
 }
 
+// rows of `width` elements stored with pitch `pitch` -> packed host array
+template <typename T>
+static bool copy_rows(T *dst, const char *src, size_t width, size_t pitch, size_t rows) {
+  if (!dst || width == 0 || rows == 0) return true;
+  return cudaMemcpy2D(dst, sizeof(T) * width, src, sizeof(T) * pitch, sizeof(T) * width, rows,
+                      cudaMemcpyDeviceToHost) == cudaSuccess;
+}
+
 extern "C" int hcran_get(hcran_t h, int32_t index, hcran_result *out) {
   if (!h || !out || index < 0 || index >= h->n) return HCRAN_EINVAL;
   int rc = sync_last(h);
@@ -277,14 +295,15 @@ extern "C" int hcran_get(hcran_t h, int32_t index, hcran_result *out) {
   InstOut o;
   bool ok = cudaMemcpy(&o, ws + h->ws.outs + sizeof(InstOut) * index, sizeof(InstOut),
                        cudaMemcpyDeviceToHost) == cudaSuccess;
+  const size_t Up = slot_stride(d.M, d.l), NPp = pair_stride(d.M, d.l);
   ok = ok && copy_out(out->A, ib + sizeof(int32_t) * il.A, d.K);
-  ok = ok && copy_out(out->S, ib + sizeof(int32_t) * il.S, d.L);
-  ok = ok && copy_out(out->p, fb + sizeof(float) * fl.p, d.L);
-  ok = ok && copy_out(out->alpha, fb + sizeof(float) * fl.alpha, d.L);
-  ok = ok && copy_out(out->beta, fb + sizeof(float) * fl.beta, d.L);
+  ok = ok && copy_rows(out->S, ib + sizeof(int32_t) * il.S, d.U, Up, d.N);
+  ok = ok && copy_rows(out->p, fb + sizeof(float) * fl.p, d.U, Up, d.N);
+  ok = ok && copy_rows(out->alpha, fb + sizeof(float) * fl.alpha, d.U, Up, d.N);
+  ok = ok && copy_rows(out->beta, fb + sizeof(float) * fl.beta, d.U, Up, d.N);
   ok = ok && copy_out(out->xi, db + sizeof(double) * dl.xi, d.M);
   ok = ok && copy_out(out->zeta, db + sizeof(double) * dl.zeta, d.Ks);
-  ok = ok && copy_out(out->zeta_sic, db + sizeof(double) * dl.zsic, size_t(d.N) * d.M * d.npair);
+  ok = ok && copy_rows(out->zeta_sic, db + sizeof(double) * dl.zsic, size_t(d.M) * d.npair, NPp, d.N);
   if (!ok) return HCRAN_ECUDA;
   out->ee = o.ee; out->R = o.R; out->P = o.P;
   out->iters[0] = o.iters[0]; out->iters[1] = o.iters[1]; out->iters[2] = o.iters[2];
@@ -316,6 +335,19 @@ extern "C" int hcran_get_summary(hcran_t h, double *ee, double *R, double *P, in
     if (min_margin) min_margin[b] = o.min_margin;
     if (n_ties) n_ties[b] = o.n_ties;
   }
+  return HCRAN_OK;
+}
+
+extern "C" int hcran_get_phase_cycles(hcran_t h, int64_t *cycles) {
+  if (!h || !cycles) return HCRAN_EINVAL;
+  int rc = sync_last(h);
+  if (rc != HCRAN_OK) return rc;
+  const char *ws = static_cast<const char *>(h->last_ws);
+  if (cudaMemcpy(h->outs_host.data(), ws + h->ws.outs, sizeof(InstOut) * h->n,
+                 cudaMemcpyDeviceToHost) != cudaSuccess)
+    return HCRAN_ECUDA;
+  for (int32_t b = 0; b < h->n; b++)
+    for (int i = 0; i < 8; i++) cycles[8 * b + i] = h->outs_host[b].cycles[i];
   return HCRAN_OK;
 }
 

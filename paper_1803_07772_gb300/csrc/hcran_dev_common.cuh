@@ -1,0 +1,273 @@
+// hcran_dev_common.cuh -- device-side context, shared-memory views, reductions
+// and the bulk-copy / mbarrier primitives used by the solver (internal).
+#pragma once
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "hcran_layout.h"
+
+namespace hcran {
+
+#define LN2F 0.69314718f
+#define LN2D 0.69314718055994530942
+
+constexpr float kPFloorRel = 1e-9f;
+constexpr float kGammaFloor = 1e-12f;
+constexpr float kInvLn2 = 1.44269504f;
+constexpr double kZetaAsumMin = 0.05;
+constexpr double kZetaMin = 1e-6, kZetaMax = 1e6;
+constexpr int kSpinLimit = 1 << 22;  // bound on every mbarrier wait
+constexpr int kStatusTimeout = 16;   // per-instance status bit: a bounded wait gave up
+
+struct Ctx {
+  int M, N, K, Ks, Ke, l, U, Up, NPp, npair, nchunk;
+  const float *G;  // Gamma[n][m][k]
+  const double *pmax, *eta, *mask, *Psi, *w;
+  double *xi, *zeta, *zsic, *zsic_next;
+  float *p, *plin, *pstart, *alpha, *beta, *pi, *gam, *X, *Aden, *Bnum, *Cnum, *slab, *SICp, *SICm,
+      *Ptot, *cu, *cp, *cX, *ckey, *Upart, *wf, *gown, *ginv;
+  int *A, *Anew, *S, *uslot;
+  float sigma;
+  double Pconst;
+};
+
+struct Shared {
+  float maskf[kMaxM], invmask[kMaxM], floorf[kMaxM], qeta[kMaxM], xif[kMaxM], fac[kMaxM],
+      sicscale[kMaxM];
+  unsigned char slot_m[kMaxU], slot_s[kMaxU];  // RRH and SIC rank of slot u
+  int pio_chunks;                              // lanes per slab row in the price sums
+  unsigned char pio_j[32], pio_ch[32];         // lane -> (row, chunk)
+  unsigned char item_m[kMaxItems], item_a[kMaxItems], item_b[kMaxItems];  // pair item -> RRH, slots
+  double redd[kWarps];
+  float redf[kWarps];
+  int redi[kWarps];
+  unsigned long long bar[kWarps][2];  // per-warp mbarriers of the two staging buffers
+  int inst;
+  int abort;
+  float min_margin;
+  int n_ties;
+};
+
+// One subcarrier's inputs: in a shared staging buffer or straight in global memory.
+struct SubView {
+  const double *z;    // [NPp] SIC multipliers the step starts from
+  const float *slab;  // [M][Up] gains from every RRH, own-RRH entry of each slot zeroed
+  const int *k;       // [Up] user per slot, -1 = empty
+  const float *p, *A, *B, *C, *alpha, *beta, *plin, *gown, *ginv;  // [Up]
+};
+
+// per-warp working buffers (dynamic shared memory)
+struct WarpBuf {
+  float *p, *pi, *X;               // [Upmax] per slot of the current subcarrier
+  int *k;                          // [Upmax]
+  float *Pt, *pio, *Sp, *Sm, *wp;  // [Mmax]
+  float *zs;                       // [Mmax * NPmax] nonzero SIC multipliers (compact)
+  int *zl;                         // [Mmax * NPmax] their pair items
+  float *part;                     // [32] per-lane partial sums
+  float *wr, *wa;                  // [KSmax] streaming rate / alpha partials
+  float *stage[2];                 // staging buffers (staged mode)
+};
+
+__device__ __forceinline__ WarpBuf warp_buf(float *dyn, const KDims &kd, int warp) {
+  float *b = dyn + (size_t)warp * warp_buf_floats(kd);
+  WarpBuf w;
+  if (kd.staged) {  // staging buffers first: 16-byte aligned
+    w.stage[0] = b;
+    w.stage[1] = b + stage_buf_floats(kd);
+    b += 2 * stage_buf_floats(kd);
+  } else {
+    w.stage[0] = w.stage[1] = nullptr;
+  }
+  w.p = b; b += kd.Upmax;
+  w.pi = b; b += kd.Upmax;
+  w.X = b; b += kd.Upmax;
+  w.k = reinterpret_cast<int *>(b); b += kd.Upmax;
+  w.Pt = b; b += kd.Mmax;
+  w.pio = b; b += kd.Mmax;
+  w.Sp = b; b += kd.Mmax;
+  w.Sm = b; b += kd.Mmax;
+  w.wp = b; b += kd.Mmax;
+  b += kd.Mmax;  // spare
+  w.zs = b; b += kd.Mmax * (kd.NPmax > 0 ? kd.NPmax : 1);
+  w.zl = reinterpret_cast<int *>(b); b += kd.Mmax * (kd.NPmax > 0 ? kd.NPmax : 1);
+  w.part = b; b += 32;
+  w.wr = b; b += (kd.KSmax > 0 ? kd.KSmax : 1);
+  w.wa = b;
+  return w;
+}
+
+// view of staging buffer `buf` laid out as stage_buf_floats describes
+__device__ __forceinline__ SubView staged_view(const float *buf, const KDims &kd, int M, int Up) {
+  SubView v;
+  v.z = reinterpret_cast<const double *>(buf);
+  const float *f = buf + 2 * kd.NPPmax;
+  v.slab = f; f += kd.Mmax * kd.Upmax;
+  v.k = reinterpret_cast<const int *>(f); f += kd.Upmax;
+  v.p = f; f += kd.Upmax;
+  v.A = f; f += kd.Upmax;
+  v.B = f; f += kd.Upmax;
+  v.C = f; f += kd.Upmax;
+  v.alpha = f; f += kd.Upmax;
+  v.beta = f; f += kd.Upmax;
+  v.plin = f; f += kd.Upmax;
+  v.gown = f; f += kd.Upmax;
+  v.ginv = f;
+  (void)M;
+  (void)Up;
+  return v;
+}
+
+// view of subcarrier n in global memory
+__device__ __forceinline__ SubView global_view(const Ctx &c, int n, const double *zsrc) {
+  SubView v;
+  const size_t o = (size_t)n * c.Up;
+  v.z = zsrc + (size_t)n * c.NPp;
+  v.slab = c.slab + (size_t)n * c.M * c.Up;
+  v.k = c.S + o;
+  v.p = c.p + o;
+  v.A = c.Aden + o;
+  v.B = c.Bnum + o;
+  v.C = c.Cnum + o;
+  v.alpha = c.alpha + o;
+  v.beta = c.beta + o;
+  v.plin = c.plin + o;
+  v.gown = c.gown + o;
+  v.ginv = c.ginv + o;
+  return v;
+}
+
+// ------------------------------------------------------------------ bulk copy + mbarrier (PTX)
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// order this thread's earlier generic-proxy accesses before later bulk copies
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+// one-dimensional bulk copy global -> shared (16-byte aligned, size % 16 == 0)
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes,
+                                         unsigned long long *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait; returns false when the limit was reached
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, uint32_t parity) {
+  for (int i = 0; i < kSpinLimit; i++)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+// FP32 reciprocal of the fast division (max 2 ulp); every divisor is a
+// positive normal number in the solver's ranges
+__device__ __forceinline__ float fast_rcp(float x) { return __fdividef(1.f, x); }
+
+// ------------------------------------------------------------------ reductions
+
+__device__ __forceinline__ float warp_sum(float v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float warp_max(float v) {
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ float warp_min(float v) {
+  for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ int warp_isum(int v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// block reductions: fixed tree, result broadcast to every thread
+__device__ inline double block_sum(double v, Shared &sh) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  v = warp_sum(v);
+  if (lane == 0) sh.redd[warp] = v;
+  __syncthreads();
+  double t = 0.0;
+  for (int i = 0; i < kWarps; i++) t += sh.redd[i];
+  __syncthreads();
+  return t;
+}
+__device__ inline float block_max(float v, Shared &sh) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  v = warp_max(v);
+  if (lane == 0) sh.redf[warp] = v;
+  __syncthreads();
+  float t = sh.redf[0];
+  for (int i = 1; i < kWarps; i++) t = fmaxf(t, sh.redf[i]);
+  __syncthreads();
+  return t;
+}
+__device__ inline float block_min(float v, Shared &sh) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  v = warp_min(v);
+  if (lane == 0) sh.redf[warp] = v;
+  __syncthreads();
+  float t = sh.redf[0];
+  for (int i = 1; i < kWarps; i++) t = fminf(t, sh.redf[i]);
+  __syncthreads();
+  return t;
+}
+__device__ inline int block_isum(int v, Shared &sh) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  v = warp_isum(v);
+  if (lane == 0) sh.redi[warp] = v;
+  __syncthreads();
+  int t = 0;
+  for (int i = 0; i < kWarps; i++) t += sh.redi[i];
+  __syncthreads();
+  return t;
+}
+
+// ------------------------------------------------------------------ model helpers
+
+__device__ __forceinline__ float gain(const Ctx &c, int n, int m, int k) {
+  return __ldg(c.G + ((size_t)n * c.M + m) * c.K + k);
+}
+// slab[n][j][u] = Gamma_{j, user in slot u}^{(n)}
+__device__ __forceinline__ float sgain(const Ctx &c, int n, int j, int u) {
+  return c.slab[((size_t)n * c.M + j) * c.Up + u];
+}
+// SIC order on (m,n): user a decoded after (is stronger than) user b
+__device__ __forceinline__ bool stronger(float ga, int a, float gb, int b) {
+  return ga > gb || (ga == gb && a < b);
+}
+__device__ __forceinline__ float weight_c(const Ctx &c, const float *szeta, int m, int k) {
+  const float w = c.wf[m * c.K + k];
+  return k >= c.Ke ? szeta[k - c.Ke] * w : w;
+}
+__device__ __forceinline__ void track(float margin, float eps, float &mm, int &nt) {
+  mm = fminf(mm, margin);
+  if (margin < eps) nt++;
+}
+
+}  // namespace hcran

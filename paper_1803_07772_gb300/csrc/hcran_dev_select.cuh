@@ -1,0 +1,341 @@
+// hcran_dev_select.cuh -- RRH / subcarrier / NOMA selection and the initial
+// point (internal).  Selection is the explicit form of the binaries of C1, C2,
+// C5, C6 once C10/C11 are relaxed with rho -> 0: at the current prices, the
+// water-filling utility of every (m, k, n) decides A_k = argmax_m sum_n u,
+// then each (m, n) admits users of m greedily by utility while the set stays
+// SIC-feasible (C14) and has at most l members.
+#pragma once
+#include "hcran_dev_dual.cuh"
+
+namespace hcran {
+
+// Water-filling candidate of user k on (m, n) at the current prices:
+// maximise c log2(1 + g p) - den p on [0, mask].
+__device__ float cand_utility(const Ctx &c, const Shared &sh, const float *szeta, int n, int m, int k,
+                              float *ps_out, float *X_out, float *key_out) {
+  const int a = c.A[k];
+  float pk = 0.f;
+  if (a >= 0) {
+    const int u = c.uslot[(size_t)k * c.N + n];
+    if (u >= 0) pk = c.p[n * c.Up + u];
+  }
+  float X = 0.f;
+  for (int j = 0; j < c.M; j++)
+    if (j != m) X += gain(c, n, j, k) * (c.Ptot[n * c.M + j] - (j == a ? pk : 0.f));
+  const float gk = gain(c, n, m, k);
+  float Y = 0.f, Pi = 0.f;
+  for (int j = 0; j < c.M; j++)
+    for (int b = 0; b < c.l; b++) {
+      const int ub = j * c.l + b;
+      const int v = c.S[n * c.Up + ub];
+      if (v < 0) break;
+      if (v == k) continue;
+      if (j != m) {
+        Pi += c.pi[n * c.Up + ub] * sgain(c, n, m, ub);
+      } else {
+        const float gv = c.gown[n * c.Up + ub];
+        if (stronger(gv, v, gk, k)) Y += c.p[n * c.Up + ub];
+        else Pi += c.pi[n * c.Up + ub] * gv;
+      }
+    }
+  const float g = gk / (c.sigma + X + gk * Y);
+  const float den = (k < c.Ke ? sh.qeta[m] : 0.f) + sh.xif[m] + Pi + c.SICp[n * c.M + m];
+  const float cw = weight_c(c, szeta, m, k);
+  const float mk = sh.maskf[m];
+  float ps;
+  if (cw <= 0.f) ps = 0.f;
+  else if (den <= 0.f) ps = mk;
+  else {
+    const float x = cw / (LN2F * den) - 1.f / g;
+    ps = x <= 0.f ? 0.f : (x >= mk ? mk : x);
+  }
+  const float u = ps > 0.f ? cw * (log1pf(g * ps) / LN2F) - den * ps : 0.f;
+  if (ps_out) {
+    *ps_out = ps;
+    *X_out = X;
+    *key_out = (cw > 0.f && den > 0.f) ? fabsf(cw * g - LN2F * den) / fmaxf(cw * g, LN2F * den) : 1.f;
+  }
+  return u;
+}
+
+// repack the gains of the selected users: slab[n][j][u] = Gamma_{j, S[n][u]}^{(n)}
+// for the RRHs j other than the slot's own, gown/ginv = the serving gain and its reciprocal
+__device__ void build_slab(const Ctx &c) {
+  for (int t = threadIdx.x; t < c.K * c.N; t += kThreads) c.uslot[t] = -1;
+  __syncthreads();
+  for (int e = threadIdx.x; e < c.N * c.Up; e += kThreads) {
+    const int k = c.S[e];
+    if (k >= 0) c.uslot[(size_t)k * c.N + e / c.Up] = e % c.Up;
+  }
+  const int MU = c.M * c.Up;
+  for (int t = threadIdx.x; t < c.N * MU; t += kThreads) {
+    const int n = t / MU, r = t - n * MU, j = r / c.Up, u = r - j * c.Up;
+    const int k = u < c.U ? c.S[n * c.Up + u] : -1;
+    const bool own = u < c.U && j == u / c.l;
+    c.slab[t] = (k >= 0 && !own) ? gain(c, n, j, k) : 0.f;
+  }
+  for (int e = threadIdx.x; e < c.N * c.Up; e += kThreads) {
+    const int k = c.S[e], u = e % c.Up;
+    const float g = k >= 0 ? gain(c, e / c.Up, u / c.l, k) : 0.f;
+    c.gown[e] = g;
+    c.ginv[e] = k >= 0 ? 1.f / g : 0.f;
+  }
+  __syncthreads();
+}
+
+// next candidate of (m, n) in (utility desc, user asc) order after (lu, lk)
+__device__ int next_candidate(const Ctx &c, int n, int m, float lu, int lk, float &bu) {
+  int bk = -1;
+  bu = 0.f;
+  const float *un = c.cu + (size_t)n * c.K;
+  for (int k = 0; k < c.K; k++) {
+    if (c.Anew[k] != m) continue;
+    const float u = un[k];
+    if (!(u < lu || (u == lu && k > lk))) continue;
+    if (bk < 0 || u > bu || (u == bu && k < bk)) {
+      bu = u;
+      bk = k;
+    }
+  }
+  return bk;
+}
+
+// greedy SIC-feasible admission on (n, m); rewrites the slots of (n, m) in place
+__device__ bool admit(const Ctx &c, int n, int m, float tie_eps, float &mm, int &nt) {
+  int chosen[kMaxL];
+  int nc = 0;
+  float lu = INFINITY, bu;
+  int lk = -1;
+  while (nc < c.l) {
+    const int bk = next_candidate(c, n, m, lu, lk, bu);
+    if (bk < 0) break;
+    lu = bu;
+    lk = bk;
+    track(c.ckey[(size_t)n * c.K + bk], tie_eps, mm, nt);
+    if (!(bu > 0.f)) break;
+    bool feasible = true;
+    const float gk = gain(c, n, m, bk);
+    for (int i = 0; i < nc && feasible; i++) {
+      const int o = chosen[i];
+      const float go = gain(c, n, m, o);
+      const bool kfirst = stronger(gk, bk, go, o);
+      const int a = kfirst ? bk : o, b = kfirst ? o : bk;
+      const float ga = kfirst ? gk : go, gb = kfirst ? go : gk;
+      const float ra = (c.sigma + c.cX[(size_t)n * c.K + a]) / ga;
+      const float rb = (c.sigma + c.cX[(size_t)n * c.K + b]) / gb;
+      track(fabsf(ra - rb) / fmaxf(ra, rb), tie_eps, mm, nt);
+      if (ra - rb > 0.f) feasible = false;  // Omega_bar > 0: SIC would fail
+    }
+    if (feasible) chosen[nc++] = bk;
+  }
+  if (nc == c.l) {  // first user left out by the cap
+    float bu2;
+    const int k2 = next_candidate(c, n, m, lu, lk, bu2);
+    const float ul = c.cu[(size_t)n * c.K + chosen[c.l - 1]];
+    if (k2 >= 0 && bu2 > 0.f) track((ul - bu2) / ul, tie_eps, mm, nt);
+  }
+  // SIC order: gain descending, lower id first
+  float cg[kMaxL];
+  for (int i = 0; i < nc; i++) cg[i] = gain(c, n, m, chosen[i]);
+  for (int i = 1; i < nc; i++) {
+    const int x = chosen[i];
+    const float gx = cg[i];
+    int j = i - 1;
+    while (j >= 0 && stronger(gx, x, cg[j], chosen[j])) {
+      chosen[j + 1] = chosen[j];
+      cg[j + 1] = cg[j];
+      j--;
+    }
+    chosen[j + 1] = x;
+    cg[j + 1] = gx;
+  }
+  const int base = n * c.Up + m * c.l;
+  int oldk[kMaxL];
+  float oldp[kMaxL], oldl[kMaxL];
+  bool same = true;
+  for (int s = 0; s < c.l; s++) {
+    oldk[s] = c.S[base + s];
+    oldp[s] = c.p[base + s];
+    oldl[s] = c.plin[base + s];
+    if (oldk[s] != (s < nc ? chosen[s] : -1)) same = false;
+  }
+  for (int s = 0; s < c.l; s++) {
+    const int e = base + s;
+    if (s >= nc) {
+      c.S[e] = -1;
+      c.p[e] = 0.f;
+      c.plin[e] = 0.f;
+    } else {
+      const int k = chosen[s];
+      int old = -1;
+      for (int b = 0; b < c.l; b++)
+        if (oldk[b] == k) old = b;
+      c.S[e] = k;
+      if (old >= 0) {  // kept links keep their power
+        c.p[e] = oldp[old];
+        c.plin[e] = oldl[old];
+      } else {  // new links start at the water-filling power
+        c.p[e] = c.cp[(size_t)n * c.K + k];
+        c.plin[e] = c.p[e];
+      }
+    }
+    c.alpha[e] = 1.f;
+    c.beta[e] = 0.f;
+  }
+  if (!same)
+    for (int pr = 0; pr < c.npair; pr++) c.zsic[(size_t)n * c.NPp + m * c.npair + pr] = 0.0;
+  return !same;
+}
+
+// Returns 1 when the selection changed.
+__device__ int selection(const Ctx &c, Shared &sh, float *dyn, const KDims &kd, const float *szeta,
+                         float tie_eps, unsigned &phase, unsigned &pending) {
+  link_all<kLinkOnly>(c, sh, dyn, kd, szeta, 0.f, phase, pending);  // prices, totals, SIC sums
+  float mm = 1.f;
+  int nt = 0;
+  // (A) per-chunk sums over n of the candidate utilities
+  const int nch = c.nchunk;
+  for (int t = threadIdx.x; t < nch * c.K; t += kThreads) {
+    const int ch = t / c.K, k = t - ch * c.K;
+    const int n0 = (int)((int64_t)c.N * ch / nch), n1 = (int)((int64_t)c.N * (ch + 1) / nch);
+    float *up = c.Upart + (size_t)ch * c.M * c.K + k;
+    for (int m = 0; m < c.M; m++) {
+      float acc = 0.f;
+      for (int n = n0; n < n1; n++) acc += cand_utility(c, sh, szeta, n, m, k, nullptr, nullptr, nullptr);
+      up[(size_t)m * c.K] = acc;
+    }
+  }
+  __syncthreads();
+  // (B) A_k = argmax_m sum_n u, lowest m on equal sums, -1 when all zero
+  int ch_local = 0;
+  for (int k = threadIdx.x; k < c.K; k += kThreads) {
+    int best = -1;
+    float b1 = 0.f, b2 = 0.f;
+    for (int m = 0; m < c.M; m++) {
+      float U = 0.f;
+      for (int ch = 0; ch < nch; ch++) U += c.Upart[((size_t)ch * c.M + m) * c.K + k];
+      if (U > b1) {
+        b2 = b1;
+        b1 = U;
+        best = m;
+      } else if (U > b2) {
+        b2 = U;
+      }
+    }
+    if (best >= 0 && b2 > 0.f) track((b1 - b2) / b1, tie_eps, mm, nt);
+    c.Anew[k] = best;
+    if (best != c.A[k]) ch_local = 1;
+  }
+  __syncthreads();
+  // (C) the candidate of every (n, k) on its chosen RRH
+  for (int t = threadIdx.x; t < c.N * c.K; t += kThreads) {
+    const int n = t / c.K, k = t - n * c.K;
+    const int m = c.Anew[k];
+    if (m < 0) {
+      c.cu[t] = 0.f;
+      c.cp[t] = 0.f;
+      c.cX[t] = 0.f;
+      c.ckey[t] = 1.f;
+      continue;
+    }
+    float ps, X, key;
+    c.cu[t] = cand_utility(c, sh, szeta, n, m, k, &ps, &X, &key);
+    c.cp[t] = ps;
+    c.cX[t] = X;
+    c.ckey[t] = key;
+  }
+  __syncthreads();
+  // (D) admission per (n, m)
+  for (int nm = threadIdx.x; nm < c.N * c.M; nm += kThreads)
+    if (admit(c, nm / c.M, nm % c.M, tie_eps, mm, nt)) ch_local = 1;
+  __syncthreads();
+  for (int k = threadIdx.x; k < c.K; k += kThreads) c.A[k] = c.Anew[k];
+  __syncthreads();
+  build_slab(c);
+  // fold decision margins and the change flag
+  const float bm = block_min(mm, sh);
+  const int bt = block_isum(nt, sh);
+  const int anych = block_isum(ch_local, sh);
+  if (threadIdx.x == 0) {
+    sh.min_margin = fminf(sh.min_margin, bm);
+    sh.n_ties += bt;
+  }
+  __syncthreads();
+  return anych > 0;
+}
+
+// p^0: A_k = argmax_m sum_n Gamma, the l strongest users of m on every
+// subcarrier (already in SIC order), p = mask / l; xi' = 0, zeta' = 1.
+__device__ void initial_state(const Ctx &c, float *szeta) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int e = threadIdx.x; e < c.N * c.Up; e += kThreads) {
+    c.S[e] = -1;
+    c.p[e] = 0.f;
+    c.plin[e] = 0.f;
+    c.alpha[e] = 1.f;
+    c.beta[e] = 0.f;
+  }
+  for (int k = threadIdx.x; k < c.K; k += kThreads) {
+    int best = 0;
+    float bv = -1.f;
+    for (int m = 0; m < c.M; m++) {
+      float t = 0.f;
+      for (int n = 0; n < c.N; n++) t += gain(c, n, m, k);
+      if (t > bv) {
+        bv = t;
+        best = m;
+      }
+    }
+    c.A[k] = best;
+  }
+  __syncthreads();
+  for (int nm = warp; nm < c.N * c.M; nm += kWarps) {
+    const int n = nm / c.M, m = nm - n * c.M;
+    float pg = INFINITY;
+    int pk = -1;
+    const float p0 = (float)(c.mask[m] / c.l);
+    for (int s = 0; s < c.l; s++) {
+      float bg = -1.f;
+      int bk = -1;
+      for (int k = lane; k < c.K; k += 32) {
+        if (c.A[k] != m) continue;
+        const float g = gain(c, n, m, k);
+        if (!(g < pg || (g == pg && k > pk))) continue;
+        if (bk < 0 || stronger(g, k, bg, bk)) {
+          bg = g;
+          bk = k;
+        }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const float og = __shfl_xor_sync(0xffffffffu, bg, o);
+        const int ok = __shfl_xor_sync(0xffffffffu, bk, o);
+        if (ok >= 0 && (bk < 0 || stronger(og, ok, bg, bk))) {
+          bg = og;
+          bk = ok;
+        }
+      }
+      if (bk < 0) break;
+      if (lane == 0) {
+        const int e = n * c.Up + m * c.l + s;
+        c.S[e] = bk;
+        c.p[e] = p0;
+        c.plin[e] = p0;
+      }
+      pg = bg;
+      pk = bk;
+    }
+  }
+  for (int m = threadIdx.x; m < c.M; m += kThreads) c.xi[m] = 0.0;
+  for (int k = threadIdx.x; k < c.Ks; k += kThreads) {
+    c.zeta[k] = 1.0;
+    szeta[k] = 1.f;
+  }
+  for (int t = threadIdx.x; t < c.N * c.NPp; t += kThreads) {
+    c.zsic[t] = 0.0;
+    c.zsic_next[t] = 0.0;
+  }
+  __syncthreads();
+  build_slab(c);
+}
+
+}  // namespace hcran

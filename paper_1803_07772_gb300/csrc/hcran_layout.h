@@ -1,5 +1,12 @@
 // hcran_layout.h -- workspace layout shared by the host planner and the
 // device solver (internal; not part of the C ABI).
+//
+// Every per-subcarrier segment of the solver state is padded to a multiple of
+// 16 bytes, so one bulk asynchronous copy (cp.async.bulk) can move it between
+// global and shared memory:
+//   slot arrays      [n][Up]        Up  = M*l rounded up to 4 floats
+//   compact slab     [n][j][Up]     gains of the selected users from RRH j
+//   SIC multipliers  [n][NPp]       NPp = M*l(l-1)/2 rounded up to 2 doubles
 #pragma once
 #include <stdint.h>
 
@@ -15,8 +22,20 @@ constexpr int kThreads = 512;          // threads per CTA (one CTA solves one in
 constexpr int kWarps = kThreads / 32;
 constexpr int kMaxM = 64;              // RRHs per instance
 constexpr int kMaxL = 8;               // NOMA users per (RRH, subcarrier)
+constexpr int kMaxU = 256;             // slots per subcarrier, M * l
+constexpr int kMaxItems = kMaxM * kMaxL * (kMaxL - 1) / 2;  // SIC pairs per subcarrier
+constexpr int kMaxDynSmem = 212 * 1024;
 
 HCRAN_HD int64_t al4(int64_t x) { return (x + 3) & ~int64_t(3); }
+HCRAN_HD int64_t al2(int64_t x) { return (x + 1) & ~int64_t(1); }
+
+// slots per subcarrier rounded up to 4 floats (row stride of slot arrays and slab)
+HCRAN_HD int slot_stride(int M, int l) { return int(al4(int64_t(M) * l)); }
+// SIC multipliers per subcarrier rounded up to 2 doubles
+HCRAN_HD int pair_stride(int M, int l) {
+  const int np = l * (l - 1) / 2;
+  return int(al2(int64_t(M) * (np > 0 ? np : 1)));
+}
 
 // per-instance descriptor (device copy lives at the start of the workspace)
 struct InstDesc {
@@ -31,12 +50,12 @@ struct InstDesc {
 
 // double arena of one instance
 struct DLayout {
-  int64_t pmax, eta, mask, Psi, w, xi, zeta, zsic, total;
+  int64_t pmax, eta, mask, Psi, w, xi, zeta, zsic, zsic_next, total;
 };
 HCRAN_HD DLayout dlayout(int M, int N, int K, int Ks, int l) {
   DLayout d;
   int64_t o = 0;
-  const int npair = l * (l - 1) / 2;
+  const int64_t NZ = int64_t(N) * pair_stride(M, l);
   d.pmax = o; o = al4(o + M);
   d.eta = o; o = al4(o + M);
   d.mask = o; o = al4(o + M);
@@ -44,20 +63,21 @@ HCRAN_HD DLayout dlayout(int M, int N, int K, int Ks, int l) {
   d.w = o; o = al4(o + int64_t(M) * K);
   d.xi = o; o = al4(o + M);
   d.zeta = o; o = al4(o + (Ks > 0 ? Ks : 1));
-  d.zsic = o; o = al4(o + int64_t(N) * M * (npair > 0 ? npair : 1));
+  d.zsic = o; o = al4(o + NZ);
+  d.zsic_next = o; o = al4(o + NZ);
   d.total = o;
   return d;
 }
 
-// float arena of one instance (L = N*U slots, U = M*l slots per subcarrier)
+// float arena of one instance (slot arrays are [n][Up])
 struct FLayout {
-  int64_t p, plin, pstart, alpha, beta, pi, gam, X, slab, SICp, SICm, Ptot, cu, cp, cX, ckey, Upart,
-      total;
+  int64_t p, plin, pstart, alpha, beta, pi, gam, X, Aden, Bnum, Cnum, gown, ginv, slab, SICp, SICm,
+      Ptot, cu, cp, cX, ckey, Upart, wf, total;
 };
 HCRAN_HD FLayout flayout(int M, int N, int K, int l, int nchunk) {
   FLayout f;
   int64_t o = 0;
-  const int64_t L = int64_t(N) * M * l;
+  const int64_t L = int64_t(N) * slot_stride(M, l);
   const int64_t NM = int64_t(N) * M, NK = int64_t(N) * K;
   f.p = o; o = al4(o + L);
   f.plin = o; o = al4(o + L);
@@ -67,7 +87,12 @@ HCRAN_HD FLayout flayout(int M, int N, int K, int l, int nchunk) {
   f.pi = o; o = al4(o + L);
   f.gam = o; o = al4(o + L);
   f.X = o; o = al4(o + L);
-  f.slab = o; o = al4(o + NM * M * l);
+  f.Aden = o; o = al4(o + L);
+  f.Bnum = o; o = al4(o + L);
+  f.Cnum = o; o = al4(o + L);
+  f.gown = o; o = al4(o + L);
+  f.ginv = o; o = al4(o + L);
+  f.slab = o; o = al4(o + NM * slot_stride(M, l));
   f.SICp = o; o = al4(o + NM);
   f.SICm = o; o = al4(o + NM);
   f.Ptot = o; o = al4(o + NM);
@@ -76,6 +101,7 @@ HCRAN_HD FLayout flayout(int M, int N, int K, int l, int nchunk) {
   f.cX = o; o = al4(o + NK);
   f.ckey = o; o = al4(o + NK);
   f.Upart = o; o = al4(o + int64_t(nchunk) * M * K);
+  f.wf = o; o = al4(o + int64_t(M) * K);
   f.total = o;
   return f;
 }
@@ -89,7 +115,7 @@ HCRAN_HD ILayout ilayout(int M, int N, int K, int l) {
   int64_t o = 0;
   i.A = o; o = al4(o + K);
   i.Anew = o; o = al4(o + K);
-  i.S = o; o = al4(o + int64_t(N) * M * l);
+  i.S = o; o = al4(o + int64_t(N) * slot_stride(M, l));
   i.uslot = o; o = al4(o + int64_t(K) * N);
   i.total = o;
   return i;
@@ -107,7 +133,36 @@ struct InstOut {
   double ee, R, P, slack_power_min, slack_rate_min, slack_sic_max, min_margin;
   int32_t iters[3];
   int32_t status, n_ties;
+  int64_t cycles[8];   // SM clock cycles per phase: selection, link, multipliers, power, scale, dinkelbach, total, pad
 };
+
+// Largest shapes of a launch; they size the per-warp shared buffers.
+struct KDims {
+  int Upmax;    // max slot stride
+  int Mmax;     // max RRHs
+  int NPmax;    // max pairs per (m, n)
+  int NPPmax;   // max pair stride per subcarrier (doubles)
+  int KSmax;    // max streaming users
+  int staged;   // 1: per-subcarrier state double-buffered in shared memory by bulk copies
+};
+// per-warp working buffers (floats)
+HCRAN_HD int warp_work_floats(const KDims &k) {
+  return 4 * k.Upmax + 6 * k.Mmax + 2 * k.Mmax * (k.NPmax > 0 ? k.NPmax : 1) + 32 +
+         2 * (k.KSmax > 0 ? k.KSmax : 1);
+}
+// one staging buffer (floats, 16-byte multiple): SIC multipliers (doubles),
+// slab rows, then the slot arrays k, p, Aden, Bnum, Cnum, alpha, beta, plin,
+// own gain and its reciprocal
+constexpr int kStagedArrays = 10;
+HCRAN_HD int stage_buf_floats(const KDims &k) {
+  return 2 * k.NPPmax + k.Mmax * k.Upmax + kStagedArrays * k.Upmax;
+}
+HCRAN_HD int warp_buf_floats(const KDims &k) {
+  return int(al4(warp_work_floats(k))) + (k.staged ? 2 * stage_buf_floats(k) : 0);
+}
+HCRAN_HD int dyn_smem_bytes(const KDims &k) {
+  return 4 * int(al4(kWarps * warp_buf_floats(k) + (k.KSmax > 0 ? k.KSmax : 1)));
+}
 
 struct Tol {
   double tol_dinkelbach, tol_scale, tol_dual;

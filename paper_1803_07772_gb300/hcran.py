@@ -58,7 +58,7 @@ class Result(C.Structure):
 
 EXPORTS = ["hcran_create", "hcran_workspace_size", "hcran_gain_elems", "hcran_prepare",
            "hcran_solve", "hcran_solve_host", "hcran_get", "hcran_get_summary",
-           "hcran_last_launch_count", "hcran_destroy"]
+           "hcran_get_phase_cycles", "hcran_last_launch_count", "hcran_destroy"]
 
 
 def load(build_if_missing: bool = True):
@@ -82,6 +82,7 @@ def load(build_if_missing: bool = True):
         "hcran_solve_host": ([vp, vp, C.POINTER(Tol), vp, vp, _dp, _ip], C.c_int),
         "hcran_get": ([vp, C.c_int32, C.POINTER(Result)], C.c_int),
         "hcran_get_summary": ([vp, _dp, _dp, _dp, _ip, _ip, _dp, _ip], C.c_int),
+        "hcran_get_phase_cycles": ([vp, _i64p], C.c_int),
         "hcran_last_launch_count": ([vp, _ip], C.c_int),
         "hcran_destroy": ([vp], None),
     }
@@ -197,6 +198,13 @@ class Solver:
                     ee=r.ee, R=r.R, P=r.P, iters=tuple(r.iters), status=r.status,
                     slack_power_min=r.slack_power_min, slack_rate_min=r.slack_rate_min,
                     slack_sic_max=r.slack_sic_max, min_margin=r.min_margin, n_ties=r.n_ties)
+
+    def phase_cycles(self) -> np.ndarray:
+        """[n, 8] SM cycles per phase of the last solve (see include/hcran.h)."""
+        out = np.zeros((len(self.instances), 8), np.int64)
+        _check("hcran_get_phase_cycles", self.lib.hcran_get_phase_cycles(
+            self.h, out.ctypes.data_as(_i64p)))
+        return out
 
     def summary(self) -> dict:
         n = len(self.instances)

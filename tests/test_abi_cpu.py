@@ -77,7 +77,7 @@ def test_create_accepts_valid_batch_and_sizes_workspace():
 
 
 @pytest.mark.parametrize("over", [dict(M=0), dict(N=0), dict(K=0), dict(Ks=-1), dict(l=0), dict(l=9),
-                                  dict(M=65), dict(Bn_hz=0.0), dict(N0_w_per_hz=-1.0),
+                                  dict(M=65), dict(M=40, l=8), dict(Bn_hz=0.0), dict(N0_w_per_hz=-1.0),
                                   dict(Bn_hz=math.nan), dict(zbar_bits=0.0)])
 def test_create_rejects_bad_scalars(over):
     inst = make_workload("small-3x8x6")[0]
