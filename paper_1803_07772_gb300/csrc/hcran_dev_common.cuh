@@ -26,7 +26,7 @@ struct Ctx {
   const double *pmax, *eta, *mask, *Psi, *w;
   double *xi, *zeta, *zsic, *zsic_next;
   float *p, *plin, *pstart, *alpha, *beta, *pi, *gam, *X, *Aden, *Bnum, *Cnum, *slab, *SICp, *SICm,
-      *Ptot, *cu, *cp, *cX, *ckey, *Upart, *wf, *gown, *ginv;
+      *Ptot, *cu, *cp, *cX, *ckey, *Upart, *wf, *gown, *ginv, *wslot;
   int *A, *Anew, *S, *uslot;
   float sigma;
   double Pconst;
@@ -54,7 +54,7 @@ struct SubView {
   const double *z;    // [NPp] SIC multipliers the step starts from
   const float *slab;  // [M][Up] gains from every RRH, own-RRH entry of each slot zeroed
   const int *k;       // [Up] user per slot, -1 = empty
-  const float *p, *A, *B, *C, *alpha, *beta, *plin, *gown, *ginv;  // [Up]
+  const float *p, *A, *B, *C, *alpha, *beta, *plin, *gown, *ginv, *w;  // [Up]
 };
 
 // per-warp working buffers (dynamic shared memory)
@@ -112,7 +112,8 @@ __device__ __forceinline__ SubView staged_view(const float *buf, const KDims &kd
   v.beta = f; f += kd.Upmax;
   v.plin = f; f += kd.Upmax;
   v.gown = f; f += kd.Upmax;
-  v.ginv = f;
+  v.ginv = f; f += kd.Upmax;
+  v.w = f;
   (void)M;
   (void)Up;
   return v;
@@ -134,6 +135,7 @@ __device__ __forceinline__ SubView global_view(const Ctx &c, int n, const double
   v.plin = c.plin + o;
   v.gown = c.gown + o;
   v.ginv = c.ginv + o;
+  v.w = c.wslot + o;
   return v;
 }
 

@@ -27,7 +27,7 @@ __device__ __forceinline__ void issue_stage(const Ctx &c, Shared &sh, const KDim
   const size_t o = (size_t)n * c.Up;
   const void *src[kStagedArrays] = {c.S + o,    c.p + o,    c.Aden + o,  c.Bnum + o,
                                     c.Cnum + o, c.alpha + o, c.beta + o, c.plin + o,
-                                    c.gown + o, c.ginv + o};
+                                    c.gown + o, c.ginv + o, c.wslot + o};
   for (int i = 0; i < kStagedArrays; i++) bulk_g2s(f + i * kd.Upmax, src[i], fa, bar);
 }
 
@@ -60,8 +60,7 @@ __device__ float sweep(const Ctx &c, Shared &sh, float *dyn, const KDims &kd, co
       const int b = i & 1;
       const int nn = n + kWarps;
       if (nn < c.N) {
-        fence_proxy_async();  // earlier reads/writes of buffer b^1 before the copy into it
-        __syncwarp();
+        __syncwarp();  // every lane is done reading buffer b^1 before the copy refills it
         if (lane == 0) issue_stage(c, sh, kd, wb.stage[b ^ 1], warp, b ^ 1, nn, zsrc);
         pending |= 2u >> b;  // bit of buffer b^1
       }

@@ -45,10 +45,11 @@ __device__ void link_subcarrier(const Ctx &c, const Shared &sh, const WarpBuf &w
       const float inv = fast_rcp(c.sigma + g_own * intra + inter);
       const float a = v.alpha[u];
       gam = wb.p[u] * g_own * inv;
-      pi = weight_c(c, szeta, m, k) * a * kInvLn2 * inv;
+      const float wk = v.w[u];
+      pi = (k >= c.Ke ? szeta[k - c.Ke] * wk : wk) * a * kInvLn2 * inv;
       if (dual && k >= c.Ke) {  // a streaming user appears at most once per subcarrier
         const int ks = k - c.Ke;
-        wb.wr[ks] += c.wf[m * c.K + k] * (a * log2f(fmaxf(gam, kGammaFloor)) + v.beta[u]);
+        wb.wr[ks] += wk * (a * log2f(fmaxf(gam, kGammaFloor)) + v.beta[u]);
         wb.wa[ks] += a;
       }
     }
@@ -154,7 +155,7 @@ __device__ void link_subcarrier(const Ctx &c, const Shared &sh, const WarpBuf &w
         float own = 0.f;  // weaker users of the same (m,n) hear this slot
         for (int b = s + 1; b < l; b++) own += wb.pi[m * l + b] * v.gown[m * l + b];
         A = wb.pio[m] + own + wb.Sp[m];
-        B = c.wf[m * c.K + k] * v.alpha[u] * kInvLn2;
+        B = v.w[u] * v.alpha[u] * kInvLn2;
         Cn = wb.Sm[m] * v.plin[u];
       }
       c.Aden[e] = A;

@@ -79,6 +79,7 @@ __device__ void build_slab(const Ctx &c) {
     const float g = k >= 0 ? gain(c, e / c.Up, u / c.l, k) : 0.f;
     c.gown[e] = g;
     c.ginv[e] = k >= 0 ? 1.f / g : 0.f;
+    c.wslot[e] = k >= 0 ? c.wf[(u / c.l) * c.K + k] : 0.f;
   }
   __syncthreads();
 }

@@ -196,6 +196,7 @@ __device__ void bind(Ctx &c, const InstDesc &d, const float *gains, double *dare
   c.wf = fb + fl.wf;
   c.gown = fb + fl.gown;
   c.ginv = fb + fl.ginv;
+  c.wslot = fb + fl.wslot;
   const ILayout il = ilayout(d.M, d.N, d.K, d.l);
   int *ib = iarena + d.i_off;
   c.A = ib + il.A; c.Anew = ib + il.Anew; c.S = ib + il.S; c.uslot = ib + il.uslot;
@@ -206,6 +207,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                  const float *__restrict__ gains, double *darena, float *farena, int *iarena,
                  InstOut *outs, Tol tol, KDims kd, int *counter) {
   __shared__ Shared sh;
+  __shared__ Ctx sc;
   extern __shared__ __align__(16) float dyn[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (lane == 0) {
@@ -222,9 +224,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncthreads();
     if (w >= n_inst) break;
     const int b = order[w];
-    Ctx c;
-    bind(c, descs[b], gains, darena, farena, iarena);
-    solve_instance(c, sh, dyn, kd, tol, outs + b, phase, pending);
+    // the instance context lives in shared memory: every field read is a
+    // shared load instead of a local-memory one
+    if (threadIdx.x == 0) bind(sc, descs[b], gains, darena, farena, iarena);
+    __syncthreads();
+    solve_instance(sc, sh, dyn, kd, tol, outs + b, phase, pending);
   }
   // never leave a bulk copy in flight (bounded; set only after a timed-out wait)
   for (int bb = 0; bb < 2; bb++)

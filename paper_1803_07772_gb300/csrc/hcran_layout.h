@@ -71,7 +71,7 @@ HCRAN_HD DLayout dlayout(int M, int N, int K, int Ks, int l) {
 
 // float arena of one instance (slot arrays are [n][Up])
 struct FLayout {
-  int64_t p, plin, pstart, alpha, beta, pi, gam, X, Aden, Bnum, Cnum, gown, ginv, slab, SICp, SICm,
+  int64_t p, plin, pstart, alpha, beta, pi, gam, X, Aden, Bnum, Cnum, gown, ginv, wslot, slab, SICp, SICm,
       Ptot, cu, cp, cX, ckey, Upart, wf, total;
 };
 HCRAN_HD FLayout flayout(int M, int N, int K, int l, int nchunk) {
@@ -92,6 +92,7 @@ HCRAN_HD FLayout flayout(int M, int N, int K, int l, int nchunk) {
   f.Cnum = o; o = al4(o + L);
   f.gown = o; o = al4(o + L);
   f.ginv = o; o = al4(o + L);
+  f.wslot = o; o = al4(o + L);
   f.slab = o; o = al4(o + NM * slot_stride(M, l));
   f.SICp = o; o = al4(o + NM);
   f.SICm = o; o = al4(o + NM);
@@ -152,8 +153,8 @@ HCRAN_HD int warp_work_floats(const KDims &k) {
 }
 // one staging buffer (floats, 16-byte multiple): SIC multipliers (doubles),
 // slab rows, then the slot arrays k, p, Aden, Bnum, Cnum, alpha, beta, plin,
-// own gain and its reciprocal
-constexpr int kStagedArrays = 10;
+// own gain and its reciprocal, priority weight w_{m,k} of the slot's link
+constexpr int kStagedArrays = 11;
 HCRAN_HD int stage_buf_floats(const KDims &k) {
   return 2 * k.NPPmax + k.Mmax * k.Upmax + kStagedArrays * k.Upmax;
 }
