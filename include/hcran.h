@@ -41,7 +41,8 @@ typedef enum {
   HCRAN_ENOMEM = 2,    /* host allocation failed or workspace too small */
   HCRAN_ECUDA = 3,     /* a CUDA runtime call failed (launch, copy, sync) */
   HCRAN_ETIMEDOUT = 4, /* reserved: a bounded device wait gave up */
-  HCRAN_ENUMERIC = 5   /* NaN/Inf reached the Dinkelbach ratio */
+  HCRAN_ENUMERIC = 5,  /* NaN/Inf reached the Dinkelbach ratio */
+  HCRAN_E2BIG = 6      /* the instance does not fit the fixed scratch of hcran_solve_noalloc */
 } hcran_status;
 
 /* per-instance result status bits */
@@ -153,6 +154,34 @@ int hcran_get_phase_cycles(hcran_t h, int64_t *cycles);
 int hcran_last_launch_count(hcran_t h, int32_t *launches);
 
 void hcran_destroy(hcran_t h);
+
+/* ---- allocation-free single-instance solve ----------------------------
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory (a process whose device memory belongs to
+ * another framework's pool or is locked after start-up, or a real-time loop
+ * that must not call the allocator because an allocation can stall on a
+ * device-wide synchronisation).  It solves one instance with the same solver
+ * kernel, using as workspace a file-scope device array of
+ * HCRAN_NOALLOC_SCRATCH_BYTES that every GPU loading this library holds
+ * until the process exits.  It calls no cudaMalloc, cudaFree or other
+ * allocating routine.
+ *  - cfg: the instance (host memory, read during the call only).
+ *  - gains_dev: float32 Gamma[n][m][k], device memory, 16-byte aligned.
+ *  - out: caller-allocated host arrays as in hcran_result (NULL skips one).
+ *  - Enqueues on `stream`, then synchronises it and copies the results; the
+ *    call returns when they are in `out`.
+ *  - The first call on a device looks up the array's device address with
+ *    that device current; make that first call before any stream capture.
+ *  - Every call on a device reuses the same array and leaves the previous
+ *    call's contents behind; the call initialises everything it reads.  Two
+ *    calls whose work overlaps on one GPU (different streams or threads)
+ *    race on the array: serialise them.
+ *  - Returns HCRAN_E2BIG, without touching the GPU, when the instance's
+ *    workspace exceeds the array (about M*N*(23*M*l + 12*K) + 30*N*M*l bytes
+ *    must stay under 16 MiB); HCRAN_EINVAL for a bad config or tolerance. */
+#define HCRAN_NOALLOC_SCRATCH_BYTES (16u << 20)
+int hcran_solve_noalloc(const hcran_config *cfg, const float *gains_dev, const hcran_tol *tol, void *stream,
+                        hcran_result *out);
 
 #ifdef __cplusplus
 }

@@ -23,7 +23,7 @@ _ip = C.POINTER(C.c_int32)
 _i64p = C.POINTER(C.c_int64)
 
 STATUS_NAMES = {0: "HCRAN_OK", 1: "HCRAN_EINVAL", 2: "HCRAN_ENOMEM", 3: "HCRAN_ECUDA",
-                4: "HCRAN_ETIMEDOUT", 5: "HCRAN_ENUMERIC"}
+                4: "HCRAN_ETIMEDOUT", 5: "HCRAN_ENUMERIC", 6: "HCRAN_E2BIG"}
 ST_NOT_CONVERGED, ST_STREAMING_UNMET, ST_EE_DECREASED, ST_NUMERIC = 1, 2, 4, 8
 
 
@@ -58,7 +58,8 @@ class Result(C.Structure):
 
 EXPORTS = ["hcran_create", "hcran_workspace_size", "hcran_gain_elems", "hcran_prepare",
            "hcran_solve", "hcran_solve_host", "hcran_get", "hcran_get_summary",
-           "hcran_get_phase_cycles", "hcran_last_launch_count", "hcran_destroy"]
+           "hcran_get_phase_cycles", "hcran_last_launch_count", "hcran_destroy",
+           "hcran_solve_noalloc"]
 
 
 def load(build_if_missing: bool = True):
@@ -85,6 +86,7 @@ def load(build_if_missing: bool = True):
         "hcran_get_phase_cycles": ([vp, _i64p], C.c_int),
         "hcran_last_launch_count": ([vp, _ip], C.c_int),
         "hcran_destroy": ([vp], None),
+        "hcran_solve_noalloc": ([C.POINTER(Config), vp, C.POINTER(Tol), vp, C.POINTER(Result)], C.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -228,3 +230,45 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+
+def solve_noalloc(inst, gains, tol: Tol, stream=None) -> dict:
+    """One instance through hcran_solve_noalloc (marshalling only).
+
+    For callers that cannot allocate device memory: the library solves in its
+    own fixed device array; `gains` is the caller's device tensor of
+    Gamma[n][m][k] (float32) and the results come back in host arrays.
+    """
+    lib = load()
+    keep = []
+
+    def d(x):
+        a = np.ascontiguousarray(x, dtype=np.float64)
+        keep.append(a)
+        return a.ctypes.data_as(_dp)
+
+    cfg = Config(inst.M, inst.N, inst.K, inst.Ks, inst.l, d(inst.pmax), d(inst.eta), d(inst.Pc),
+                 d(inst.Pf), float(inst.Bn_hz), float(inst.N0_w_per_hz),
+                 d(inst.T_s) if inst.Ks else None, d(inst.lambda_pps) if inst.Ks else None,
+                 float(inst.zbar_bits), d(inst.w) if inst.w is not None else None)
+    N, M, K, Ks, l = inst.N, inst.M, inst.K, inst.Ks, inst.l
+    L, npair = N * M * l, l * (l - 1) // 2
+    arr = dict(A=np.zeros(K, np.int32), S=np.zeros(L, np.int32), p=np.zeros(L, np.float32),
+               alpha=np.zeros(L, np.float32), beta=np.zeros(L, np.float32), xi=np.zeros(M),
+               zeta=np.zeros(max(Ks, 1)), zeta_sic=np.zeros(max(N * M * npair, 1)))
+    r = Result()
+    for k, a in arr.items():
+        t = _ip if a.dtype == np.int32 else (_fp if a.dtype == np.float32 else _dp)
+        setattr(r, k, a.ctypes.data_as(t))
+    sptr = None
+    if stream is not None:
+        sptr = C.c_void_p(stream.cuda_stream)
+    ptr = gains.data_ptr() if hasattr(gains, "data_ptr") else int(gains)
+    _check("hcran_solve_noalloc", lib.hcran_solve_noalloc(C.byref(cfg), C.c_void_p(ptr), C.byref(tol),
+                                                          sptr, C.byref(r)))
+    return dict(A=arr["A"], S=arr["S"].reshape(N, M, l), p=arr["p"].reshape(N, M, l),
+                alpha=arr["alpha"].reshape(N, M, l), beta=arr["beta"].reshape(N, M, l),
+                xi=arr["xi"], zeta=arr["zeta"][:Ks],
+                zeta_sic=arr["zeta_sic"][:N * M * npair].reshape(N, M, npair),
+                ee=r.ee, R=r.R, P=r.P, iters=tuple(r.iters), status=r.status,
+                min_margin=r.min_margin, n_ties=r.n_ties)
