@@ -252,7 +252,9 @@ def run_gpu(args):
         try:
             prof = json.load(open(os.path.join(ROOT, "profiles", "solve_kernel_traffic.json")))
             if prof.get("kernel_hash") == kernel_hash():
-                traffic = prof.get("dram_bytes_per_launch_scaled")
+                # DRAM bytes per algorithmic byte from the launch list of a smaller
+                # case of the same workload, scaled to this launch's algorithmic bytes
+                traffic = float(prof["traffic_per_algorithmic_byte"]) * abytes
         except Exception:
             pass
         out = {
@@ -287,6 +289,20 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+def run_profile_case():
+    import torch
+    from hcran_inputs import Tolerances, make_workload, pack_batch
+    from paper_1803_07772_gb300 import Solver, make_tol
+    insts = make_workload(WORKLOAD, count=152)
+    gains, offs = pack_batch(insts)
+    s = Solver(insts, gain_offsets=offs)
+    g = torch.from_numpy(gains).cuda()
+    s.solve(g, make_tol(Tolerances(max_dinkelbach=1, max_scale=2, max_dual=100)))
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": WORKLOAD, "instances": 152,
+                      "iters_total": s.summary()["iters"].sum(0).tolist()}))
+
+
 def kernel_hash() -> str:
     import hashlib
     h = hashlib.sha256()
@@ -304,7 +320,13 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--instances", type=int, default=4096)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-case", action="store_true",
+                    help="one solve of the first 152 instances with short caps (1 Dinkelbach "
+                         "iteration, 2 SCALE passes, 100 dual iterations): the small case for ncu")
     args = ap.parse_args()
+    if args.profile_case:
+        run_profile_case()
+        return
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
