@@ -338,7 +338,18 @@ typedef struct {
   double *Ptot, *Ie, *gam, *pi, *SICp, *SICm, *u, *pstar, *Xc;
   int *ids;
   double *keys;
+  double noise_rel;                 /* perturbation ensemble (orc_params), 0 = off */
+  uint64_t noise_seed, noise_ctr;
 } scratch_t;
+
+/* u uniform in [-1, 1) from the splitmix64 output of counter noise_ctr */
+static double noise_u(scratch_t *w) {
+  uint64_t z = w->noise_seed + 0x9E3779B97F4A7C15ull * (++w->noise_ctr);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  return (double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+}
 
 static void track(double margin, double eps, double *min_margin, int *n_ties) {
   if (margin < *min_margin) *min_margin = margin;
@@ -577,7 +588,7 @@ static double dual_iteration(const inst_t *I, state_t *st, double q, int v, scra
     if (st->S[e] < 0) continue;
     double d = fabs(pnew[e] - st->p[e]) / I->mask[(e / l) % M];
     if (d > dmax) dmax = d;
-    st->p[e] = pnew[e];
+    st->p[e] = w->noise_rel > 0.0 ? pnew[e] * (1.0 + w->noise_rel * noise_u(w)) : pnew[e];
   }
   return dmax;
 }
@@ -654,6 +665,9 @@ int orc_solve(const orc_problem *pr, const orc_params *par, orc_result *out) {
   w.keys = calloc(NMK, sizeof(double));
   w.Xc = calloc(NMK, sizeof(double));
   w.ids = malloc(sizeof(int) * I.K);
+  w.noise_rel = par->noise_rel;
+  w.noise_seed = par->noise_seed;
+  w.noise_ctr = 0;
   double *pstart = malloc(sizeof(double) * L);
   state_t st;
   int ok = state_alloc(&I, &st) && w.Ptot && w.Ie && w.u && w.pstar &&

@@ -37,6 +37,13 @@ typedef struct {
   int32_t max_dinkelbach, max_scale, max_dual;
   double q_init;               /* > 0: fixed E^1 (else E^1 = R(p^0)/P(p^0)) */
   double tie_eps;              /* relative margin under which a selection decision counts as a tie */
+  /* Perturbation ensemble (parity tests only; 0 = off, the default): each new
+   * power of a dual iteration is multiplied by (1 + noise_rel * u), u uniform
+   * in [-1, 1) from a splitmix64 stream keyed by noise_seed.  With noise_rel
+   * near the FP32 unit roundoff this shows where rounding-level differences
+   * can move an instance's end point. */
+  double noise_rel;
+  uint64_t noise_seed;
 } orc_params;
 
 typedef struct {

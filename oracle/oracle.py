@@ -34,7 +34,7 @@ class _Params(C.Structure):
     _fields_ = [("tol_dinkelbach", C.c_double), ("tol_scale", C.c_double),
                 ("tol_dual", C.c_double), ("max_dinkelbach", C.c_int32),
                 ("max_scale", C.c_int32), ("max_dual", C.c_int32), ("q_init", C.c_double),
-                ("tie_eps", C.c_double)]
+                ("tie_eps", C.c_double), ("noise_rel", C.c_double), ("noise_seed", C.c_uint64)]
 
 
 class _Result(C.Structure):
@@ -116,8 +116,13 @@ def _ptr(a, t):
 
 def solve(inst, tol=None, q_init: float = 0.0, tie_eps: float = 1e-9,
           max_dinkelbach: Optional[int] = None, max_scale: Optional[int] = None,
-          max_dual: Optional[int] = None) -> OracleResult:
-    """Run the oracle on one ``hcran_inputs.Instance``."""
+          max_dual: Optional[int] = None, noise_rel: float = 0.0,
+          noise_seed: int = 0) -> OracleResult:
+    """Run the oracle on one ``hcran_inputs.Instance``.
+
+    ``noise_rel > 0`` turns on the perturbation ensemble (test use only): every
+    new power of a dual iteration is scaled by (1 + noise_rel * u), u uniform
+    in [-1, 1) from a stream keyed by ``noise_seed``."""
     lib = _load()
     M, N, K, Ks, l = inst.M, inst.N, inst.K, inst.Ks, inst.l
     npair = l * (l - 1) // 2
@@ -142,7 +147,7 @@ def solve(inst, tol=None, q_init: float = 0.0, tie_eps: float = 1e-9,
     Smax = max_scale if max_scale is not None else tol.max_scale
     Vmax = max_dual if max_dual is not None else tol.max_dual
     par = _Params(tol.tol_dinkelbach, tol.tol_scale, tol.tol_dual, Imax, Smax, Vmax,
-                  q_init, tie_eps)
+                  q_init, tie_eps, float(noise_rel), int(noise_seed))
     L = N * M * l
     out = dict(A=np.zeros(K, np.int32), S=np.zeros(L, np.int32), p=np.zeros(L),
                alpha=np.zeros(L), beta=np.zeros(L), xi=np.zeros(M), zeta=np.zeros(max(Ks, 1)),

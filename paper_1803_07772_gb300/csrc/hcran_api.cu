@@ -29,7 +29,7 @@ struct hcran_s {
   std::vector<double> dimage;   // full double arena (constants + zeroed multipliers)
   int64_t gain_elems = 0, dtot = 0, ftot = 0, itot = 0;
   WsLayout ws{};
-  KDims kd{0, 0, 0, 0, 0, 0};
+  KDims kd{0, 0, 0, 0, 0, 0, 0, 0};
   void *last_ws = nullptr;
   cudaStream_t last_stream = nullptr;
   int32_t last_launches = 0;
@@ -84,7 +84,7 @@ extern "C" int hcran_create(hcran_t *out, const hcran_config *cfgs, int32_t n,
   try {
     h->n = n;
     h->descs.resize(n);
-    int64_t goff = 0, doff = 0, foff = 0, ioff = 0;
+    int64_t goff = 0, doff = 0, foff = 0, ioff = 0, res_need = 0;
     for (int32_t b = 0; b < n; b++) {
       const hcran_config &c = cfgs[b];
       InstDesc &d = h->descs[b];
@@ -118,11 +118,9 @@ extern "C" int hcran_create(hcran_t *out, const hcran_config *cfgs, int32_t n,
       h->kd.NPmax = std::max(h->kd.NPmax, d.npair);
       h->kd.NPPmax = std::max(h->kd.NPPmax, pair_stride(c.M, c.l));
       h->kd.KSmax = std::max(h->kd.KSmax, d.Ks);
+      res_need = std::max(res_need, res_floats(c.M, c.l, c.Ks, c.N));
     }
-    // stage per-subcarrier state in shared memory when the double buffers fit
-    h->kd.staged = 1;
-    if (dyn_smem_bytes(h->kd) > kMaxDynSmem) h->kd.staged = 0;
-    if (dyn_smem_bytes(h->kd) > kMaxDynSmem) { delete h; return HCRAN_EINVAL; }
+    if (plan_kdims(h->kd, res_need) != 0) { delete h; return HCRAN_EINVAL; }
     h->gain_elems = al4(h->gain_elems);
     h->dtot = doff; h->ftot = foff; h->itot = ioff;
     // constants image of the double arena

@@ -43,6 +43,7 @@ struct Shared {
   float redf[kWarps];
   int redi[kWarps];
   unsigned long long bar[kWarps][2];  // per-warp mbarriers of the two staging buffers
+  long long cyc[8];  // SM clock cycles per phase of the current instance (thread 0)
   int inst;
   int abort;
   float min_margin;
@@ -66,18 +67,18 @@ struct WarpBuf {
   int *zl;                         // [Mmax * NPmax] their pair items
   float *part;                     // [32] per-lane partial sums
   float *wr, *wa;                  // [KSmax] streaming rate / alpha partials
-  float *stage[2];                 // staging buffers (staged mode)
+  float *stage0, *stage1;          // staging buffers (staged mode)
 };
 
 __device__ __forceinline__ WarpBuf warp_buf(float *dyn, const KDims &kd, int warp) {
-  float *b = dyn + (size_t)warp * warp_buf_floats(kd);
+  float *b = dyn + dyn_head_floats(kd) + (size_t)warp * warp_stride(kd);
   WarpBuf w;
   if (kd.staged) {  // staging buffers first: 16-byte aligned
-    w.stage[0] = b;
-    w.stage[1] = b + stage_buf_floats(kd);
+    w.stage0 = b;
+    w.stage1 = b + stage_buf_floats(kd);
     b += 2 * stage_buf_floats(kd);
   } else {
-    w.stage[0] = w.stage[1] = nullptr;
+    w.stage0 = w.stage1 = nullptr;
   }
   w.p = b; b += kd.Upmax;
   w.pi = b; b += kd.Upmax;

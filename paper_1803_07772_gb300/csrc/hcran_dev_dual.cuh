@@ -51,7 +51,7 @@ __device__ float sweep(const Ctx &c, Shared &sh, float *dyn, const KDims &kd, co
   float dl = 0.f;
   int i = 0;
   if (kd.staged && warp < c.N && lane == 0) {
-    issue_stage(c, sh, kd, wb.stage[0], warp, 0, warp, zsrc);
+    issue_stage(c, sh, kd, wb.stage0, warp, 0, warp, zsrc);
     pending |= 1u;
   }
   for (int n = warp; n < c.N; n += kWarps, i++) {
@@ -61,14 +61,14 @@ __device__ float sweep(const Ctx &c, Shared &sh, float *dyn, const KDims &kd, co
       const int nn = n + kWarps;
       if (nn < c.N) {
         __syncwarp();  // every lane is done reading buffer b^1 before the copy refills it
-        if (lane == 0) issue_stage(c, sh, kd, wb.stage[b ^ 1], warp, b ^ 1, nn, zsrc);
+        if (lane == 0) issue_stage(c, sh, kd, b ? wb.stage0 : wb.stage1, warp, b ^ 1, nn, zsrc);
         pending |= 2u >> b;  // bit of buffer b^1
       }
       const bool ok = mbar_wait(&sh.bar[warp][b], (phase >> b) & 1u);
       phase ^= 1u << b;
       pending &= ~(1u << b);
       if (!ok) sh.abort = 1;
-      v = staged_view(wb.stage[b], kd, c.M, c.Up);
+      v = staged_view(b ? wb.stage1 : wb.stage0, kd, c.M, c.Up);
     } else {
       v = global_view(c, n, zsrc);
     }
@@ -104,7 +104,7 @@ __device__ int dual_loop(const Ctx &c, Shared &sh, float *dyn, const KDims &kd, 
   const int Vmax = tol.max_dual > 0 ? tol.max_dual : 1;
   const long long t0 = clock64();
   link_all<kLinkDual>(c, sh, dyn, kd, szeta, 1.f, phase, pending);  // residuals at p^0, SIC step delta_0
-  cyc[1] += clock64() - t0;
+  if (threadIdx.x == 0) cyc[1] += clock64() - t0;
   int v = 0;
   for (;;) {
     const long long t1 = clock64();
@@ -115,7 +115,7 @@ __device__ int dual_loop(const Ctx &c, Shared &sh, float *dyn, const KDims &kd, 
     // projected subgradient step on xi' (C12) and zeta' (C13 hat) at p^v:
     // steps in FP32, accumulated into the FP64 multiplier values
     const float delta = rsqrtf((float)v + 1.f);
-    const int wstride = warp_buf_floats(kd);
+    const int wstride = warp_stride(kd);
     const WarpBuf w0 = warp_buf(dyn, kd, 0);
     for (int t = threadIdx.x; t < c.M + c.Ks; t += kThreads) {
       if (t < c.M) {
@@ -152,8 +152,10 @@ __device__ int dual_loop(const Ctx &c, Shared &sh, float *dyn, const KDims &kd, 
     v++;
     __syncthreads();
     const long long t3 = clock64();
-    cyc[2] += t2 - t1;
-    cyc[3] += t3 - t2;
+    if (threadIdx.x == 0) {
+      cyc[2] += t2 - t1;
+      cyc[3] += t3 - t2;
+    }
   }
   // gamma, pi, X, totals and SIC sums at the final point for the later phases
   link_all<kLinkOnly>(c, sh, dyn, kd, szeta, 0.f, phase, pending);

@@ -5,7 +5,7 @@
 // then each (m, n) admits users of m greedily by utility while the set stays
 // SIC-feasible (C14) and has at most l members.
 #pragma once
-#include "hcran_dev_dual.cuh"
+#include "hcran_dev_resident.cuh"
 
 namespace hcran {
 

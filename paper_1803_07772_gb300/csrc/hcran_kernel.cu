@@ -21,7 +21,7 @@ namespace hcran {
 
 __device__ void solve_instance(const Ctx &c, Shared &sh, float *dyn, const KDims &kd, const Tol &tol,
                                InstOut *out, unsigned &phase, unsigned &pending) {
-  float *szeta = dyn + (size_t)kWarps * warp_buf_floats(kd);
+  float *szeta = dyn;  // streaming multipliers in FP32, first in dynamic shared memory
   for (int m = threadIdx.x; m < c.M; m += kThreads) {
     sh.maskf[m] = (float)c.mask[m];
     sh.floorf[m] = (float)c.mask[m] * kPFloorRel;
@@ -51,12 +51,13 @@ __device__ void solve_instance(const Ctx &c, Shared &sh, float *dyn, const KDims
   }
   for (int t = threadIdx.x; t < c.M * c.K; t += kThreads) c.wf[t] = (float)c.w[t];
   if (threadIdx.x == 0) {
+    for (int i = 0; i < 8; i++) sh.cyc[i] = 0;
     sh.min_margin = 1.f;
     sh.n_ties = 0;
     sh.abort = 0;
   }
   __syncthreads();
-  long long cyc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  long long *cyc = sh.cyc;  // written by thread 0 only
   const long long t_begin = clock64();
   initial_state(c, szeta);
   double R, P;
@@ -74,7 +75,7 @@ __device__ void solve_instance(const Ctx &c, Shared &sh, float *dyn, const KDims
     __syncthreads();
     const long long ta = clock64();
     selection(c, sh, dyn, kd, szeta, tol.tie_eps, phase, pending);
-    cyc[0] += clock64() - ta;
+    if (threadIdx.x == 0) cyc[0] += clock64() - ta;
     // Algorithm 1 at E^i = q (alpha = 1, beta = 0 written by the selection)
     for (int s = 0; s < Smax && !sh.abort; s++) {
       for (int e = threadIdx.x; e < c.N * c.Up; e += kThreads) {
@@ -82,7 +83,8 @@ __device__ void solve_instance(const Ctx &c, Shared &sh, float *dyn, const KDims
         c.plin[e] = c.p[e];
       }
       __syncthreads();
-      it_v += dual_loop(c, sh, dyn, kd, szeta, tol, cyc, phase, pending);
+      it_v += kd.resident ? dual_loop_res(c, sh, dyn, kd, szeta, tol, cyc, phase, pending)
+                          : dual_loop(c, sh, dyn, kd, szeta, tol, cyc, phase, pending);
       const long long t5 = clock64();
       scale_update(c);
       it_s++;
@@ -90,14 +92,14 @@ __device__ void solve_instance(const Ctx &c, Shared &sh, float *dyn, const KDims
       for (int e = threadIdx.x; e < c.N * c.Up; e += kThreads)
         if (c.S[e] >= 0) dm = fmaxf(dm, fabsf(c.p[e] - c.pstart[e]) / sh.maskf[(e % c.Up) / c.l]);
       dm = block_max(dm, sh);
-      cyc[4] += clock64() - t5;
+      if (threadIdx.x == 0) cyc[4] += clock64() - t5;
       if (dm < (float)tol.tol_scale) break;
     }
     const long long t6 = clock64();
     project_power(c, sh);
     link_all<kLinkOnly>(c, sh, dyn, kd, szeta, 0.f, phase, pending);
     exact_R_P(c, sh, R, P);
-    cyc[5] += clock64() - t6;
+    if (threadIdx.x == 0) cyc[5] += clock64() - t6;
     it_d++;
     if (!isfinite(R) || !isfinite(P) || P <= 0.0) {
       status = 8;
@@ -245,7 +247,7 @@ cudaError_t launch_solve(const InstDesc *descs, const int *order, int n_inst, co
   if (err != cudaSuccess) return err;
   err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (err != cudaSuccess) return err;
-  const int smem = dyn_smem_bytes(kd);
+  const int smem = (int)dyn_smem_bytes(kd);
   err = cudaFuncSetAttribute(solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (err != cudaSuccess) return err;
   err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, solve_kernel, kThreads, smem);

@@ -24,7 +24,7 @@ constexpr int kMaxM = 64;              // RRHs per instance
 constexpr int kMaxL = 8;               // NOMA users per (RRH, subcarrier)
 constexpr int kMaxU = 256;             // slots per subcarrier, M * l
 constexpr int kMaxItems = kMaxM * kMaxL * (kMaxL - 1) / 2;  // SIC pairs per subcarrier
-constexpr int kMaxDynSmem = 212 * 1024;
+constexpr int kMaxDynSmem = 216 * 1024;
 
 HCRAN_HD int64_t al4(int64_t x) { return (x + 3) & ~int64_t(3); }
 HCRAN_HD int64_t al2(int64_t x) { return (x + 1) & ~int64_t(1); }
@@ -145,6 +145,8 @@ struct KDims {
   int NPPmax;   // max pair stride per subcarrier (doubles)
   int KSmax;    // max streaming users
   int staged;   // 1: per-subcarrier state double-buffered in shared memory by bulk copies
+  int resident; // 1: the dual loop keeps the CTA's subcarrier state in shared memory
+  int res_floats;  // resident region (floats), the largest instance of the launch
 };
 // per-warp working buffers (floats)
 HCRAN_HD int warp_work_floats(const KDims &k) {
@@ -161,8 +163,64 @@ HCRAN_HD int stage_buf_floats(const KDims &k) {
 HCRAN_HD int warp_buf_floats(const KDims &k) {
   return int(al4(warp_work_floats(k))) + (k.staged ? 2 * stage_buf_floats(k) : 0);
 }
-HCRAN_HD int dyn_smem_bytes(const KDims &k) {
-  return 4 * int(al4(kWarps * warp_buf_floats(k) + (k.KSmax > 0 ? k.KSmax : 1)));
+// Resident dual loop: shared-memory state of Nc subcarriers (structure of
+// arrays): slab [Nc][M][Rs] (row stride Rs = Up, or Up + 4 when Up / 4 is
+// even, so that lanes reading consecutive rows as float4 hit distinct banks);
+// slot arrays k, p, pi, g_own, 1/g_own, w*alpha, alpha, w*beta, p_lin, X
+// [Nc][Up]; per-RRH totals, price sums, SIC+ and SIC- [Nc][M]; SIC
+// multipliers as (hi, lo) float pairs in two generations [Nc][M*npair]; the
+// nonzero-multiplier bit masks [Nc][ceil(M*npair/32)]; the streaming rate and
+// alpha contributions [Nc][Ks].
+HCRAN_HD int res_row_stride(int M, int l) {
+  const int Up = slot_stride(M, l);
+  return ((Up / 4) & 1) ? Up : Up + 4;
+}
+constexpr int kResSlotArrays = 10;
+HCRAN_HD int64_t res_floats(int M, int l, int Ks, int Nc) {
+  const int64_t Up = slot_stride(M, l), Mi = int64_t(M) * (l * (l - 1) / 2);
+  const int64_t NW = (Mi + 31) / 32;
+  return int64_t(Nc) * M * res_row_stride(M, l) + kResSlotArrays * int64_t(Nc) * Up +
+         4 * al4(int64_t(Nc) * M) + 4 * al4(int64_t(Nc) * Mi) + al4(int64_t(Nc) * NW) +
+         2 * al4(int64_t(Nc) * Ks);
+}
+// resident scratch: cluster exchange vectors (two parities), the FP64
+// multipliers xi', zeta' of the CTA, and the constants of their steps
+// (1 / pmax_m, 1 / (ln2 mask_m), Psi_k) in FP32
+HCRAN_HD int res_xch_floats(const KDims &k) {
+  return int(al4(k.Mmax + 2 * (k.KSmax > 0 ? k.KSmax : 1) + 2));
+}
+HCRAN_HD int res_scratch_floats(const KDims &k) {
+  const int m4 = int(al4(k.Mmax)), s4 = int(al4(k.KSmax > 0 ? k.KSmax : 1));
+  return 2 * res_xch_floats(k) + 2 * m4 + 2 * s4 + 2 * m4 + s4;  // + 1/pmax, xi step scale, Psi
+}
+// Dynamic shared memory: streaming multipliers zeta' (FP32), the resident
+// scratch, then one region that holds either the per-warp buffers of the
+// other phases or, during a dual loop, the resident state.
+HCRAN_HD int64_t dyn_head_floats(const KDims &k) {
+  return al4(k.KSmax > 0 ? k.KSmax : 1) + (k.resident ? res_scratch_floats(k) : 0);
+}
+HCRAN_HD int warp_stride(const KDims &k) { return warp_buf_floats(k); }
+HCRAN_HD int64_t dyn_smem_bytes(const KDims &k) {
+  const int64_t w = int64_t(kWarps) * warp_stride(k);
+  const int64_t r = k.resident ? int64_t(k.res_floats) : 0;
+  return 4 * (dyn_head_floats(k) + (w > r ? w : r));
+}
+
+// Schedule of a launch: the resident dual loop when the largest instance's
+// state fits shared memory, else bulk-copy staging of each subcarrier when the
+// double buffers fit, else global reads.  Returns nonzero when even the
+// per-warp buffers do not fit.
+inline int plan_kdims(KDims &k, int64_t res_need) {
+  k.staged = 0;
+  k.resident = 1;
+  k.res_floats = int(res_need < (int64_t(1) << 30) ? res_need : (int64_t(1) << 30));
+  if (dyn_smem_bytes(k) <= kMaxDynSmem) return 0;
+  k.resident = 0;
+  k.res_floats = 0;
+  k.staged = 1;
+  if (dyn_smem_bytes(k) <= kMaxDynSmem) return 0;
+  k.staged = 0;
+  return dyn_smem_bytes(k) <= kMaxDynSmem ? 0 : 1;
 }
 
 struct Tol {

@@ -92,9 +92,7 @@ int plan(const hcran_config &c, Plan &p) {
   p.kd.NPmax = d.npair;
   p.kd.NPPmax = pair_stride(c.M, c.l);
   p.kd.KSmax = c.Ks;
-  p.kd.staged = 1;
-  if (dyn_smem_bytes(p.kd) > kMaxDynSmem) p.kd.staged = 0;
-  if (dyn_smem_bytes(p.kd) > kMaxDynSmem) return HCRAN_EINVAL;
+  if (plan_kdims(p.kd, res_floats(c.M, c.l, c.Ks, c.N)) != 0) return HCRAN_EINVAL;
   uint64_t o = 0;
   p.o_desc = o; o = al256(o + sizeof(InstDesc));
   p.o_order = o; o = al256(o + sizeof(int32_t));

@@ -371,3 +371,25 @@ def test_oracle_not_above_brute_force(shape, seed):
     bf = brute_force_ee(inst)
     assert r.ee <= bf * (1 + 1e-3)
     assert r.ee >= 0.5 * bf
+
+
+def test_perturbation_ensemble_is_opt_in_and_small_on_a_stable_instance():
+    """The ensemble hook is off by default (bit-identical results), a given
+    seed reproduces itself, and on an instance with a stable end point the
+    FP32-level perturbations move the EE by far less than the parity bar."""
+    from tests.oracle_ensemble import NOISE_REL, ensemble
+    name = "small-3x8x6"
+    inst = make_workload(name)[0]
+    tol = WORKLOADS[name]["tol"]
+    a = oracle.solve(inst, tol)
+    b = oracle.solve(inst, tol, noise_rel=0.0, noise_seed=99)
+    assert a.ee == b.ee and np.array_equal(a.p, b.p)
+    c1 = oracle.solve(inst, tol, noise_rel=NOISE_REL, noise_seed=3)
+    c2 = oracle.solve(inst, tol, noise_rel=NOISE_REL, noise_seed=3)
+    assert c1.ee == c2.ee and np.array_equal(c1.p, c2.p)
+    assert c1.ee != a.ee
+    members = ensemble(inst, tol, n=3)
+    assert members[0].ee == a.ee
+    for r in members[1:]:
+        assert np.array_equal(r.S, a.S)
+        assert abs(r.ee - a.ee) / a.ee < 1e-6
