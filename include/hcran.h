@@ -153,6 +153,16 @@ int hcran_get_phase_cycles(hcran_t h, int64_t *cycles);
 /* Kernel launches issued by the last hcran_solve (for accounting). */
 int hcran_last_launch_count(hcran_t h, int32_t *launches);
 
+/* Schedule chosen at hcran_create for every instance (no device access):
+ * cluster_size[b] = number of CTAs (a thread-block cluster, 1, 2, 4 or 8)
+ * that solve instance b with the dual-loop state resident in their shared
+ * memory, or 0 when that state does not fit even 8 CTAs and the instance is
+ * solved by one CTA streaming each subcarrier's state from global memory.
+ * Instances of one cluster size share one persistent launch.  cluster_size:
+ * caller-owned host array of n int32.  Returns HCRAN_EINVAL on a NULL
+ * argument. */
+int hcran_get_schedule(hcran_t h, int32_t *cluster_size);
+
 void hcran_destroy(hcran_t h);
 
 /* ---- allocation-free single-instance solve ----------------------------

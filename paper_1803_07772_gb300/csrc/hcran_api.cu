@@ -17,19 +17,27 @@
 namespace hcran {
 cudaError_t launch_solve(const InstDesc *descs, const int *order, int n_inst, const float *gains,
                          double *darena, float *farena, int *iarena, InstOut *outs, const Tol &tol,
-                         const KDims &kd, int *counter, cudaStream_t stream, int *launches);
+                         const KDims &kd, int csize, int *counter, cudaStream_t stream, int *launches);
 }
 
 using namespace hcran;
 
+// one launch: the instances of a class (cluster size) with the launch's dimensions
+struct LaunchClass {
+  int csize = 1;
+  KDims kd{0, 0, 0, 0, 0, 0, 0, 0};
+  int first = 0, count = 0;  // segment of the order array
+};
+
 struct hcran_s {
   int32_t n = 0;
   std::vector<InstDesc> descs;
-  std::vector<int32_t> order;
+  std::vector<int32_t> order;     // instances grouped by class, LPT within a class
+  std::vector<int32_t> cls;       // launch class of every instance
+  LaunchClass classes[kNumClasses];
   std::vector<double> dimage;   // full double arena (constants + zeroed multipliers)
   int64_t gain_elems = 0, dtot = 0, ftot = 0, itot = 0;
   WsLayout ws{};
-  KDims kd{0, 0, 0, 0, 0, 0, 0, 0};
   void *last_ws = nullptr;
   cudaStream_t last_stream = nullptr;
   int32_t last_launches = 0;
@@ -84,7 +92,8 @@ extern "C" int hcran_create(hcran_t *out, const hcran_config *cfgs, int32_t n,
   try {
     h->n = n;
     h->descs.resize(n);
-    int64_t goff = 0, doff = 0, foff = 0, ioff = 0, res_need = 0;
+    int64_t goff = 0, doff = 0, foff = 0, ioff = 0;
+    h->cls.resize(n);
     for (int32_t b = 0; b < n; b++) {
       const hcran_config &c = cfgs[b];
       InstDesc &d = h->descs[b];
@@ -93,7 +102,8 @@ extern "C" int hcran_create(hcran_t *out, const hcran_config *cfgs, int32_t n,
       d.U = c.M * c.l;
       d.L = c.N * d.U;
       d.npair = c.l * (c.l - 1) / 2;
-      d.nchunk = nchunk_for(c.N, c.K);
+      h->cls[b] = pick_class(c.M, c.l, c.Ks, c.N);
+      d.nchunk = class_nchunk(c.N, c.K, class_csize(h->cls[b]));
       const int64_t cost = int64_t(c.N) * c.M * c.K;
       if (gain_offsets) {
         if (gain_offsets[b] < 0 || (gain_offsets[b] & 3)) { delete h; return HCRAN_EINVAL; }
@@ -107,20 +117,56 @@ extern "C" int hcran_create(hcran_t *out, const hcran_config *cfgs, int32_t n,
       double pc = 0.0;
       for (int m = 0; m < c.M; m++) pc += c.Pc[m] + c.Pf[m];
       d.Pconst = pc;
+    }
+    // launch dimensions per class; an instance that would push its class over
+    // the shared-memory limit moves on to the next larger cluster
+    for (;;) {
+      bool moved = false;
+      for (int k = 0; k < kNumClasses; k++) h->classes[k] = LaunchClass();
+      for (int32_t b = 0; b < n; b++) {
+        const hcran_config &c = cfgs[b];
+        LaunchClass &L = h->classes[h->cls[b]];
+        const KDims one = h->cls[b] < kNumClasses - 1
+                              ? resident_kdims(c.M, c.l, c.Ks, c.N, class_csize(h->cls[b]))
+                              : KDims{slot_stride(c.M, c.l), c.M, c.l * (c.l - 1) / 2, pair_stride(c.M, c.l),
+                                      c.Ks, 0, 0, 0};
+        if (L.count == 0) L.kd = one;
+        else kdims_merge(L.kd, one);
+        L.count++;
+      }
+      for (int k = 0; k < kNumClasses - 1 && !moved; k++) {
+        LaunchClass &L = h->classes[k];
+        if (L.count == 0 || dyn_smem_bytes(L.kd) <= kMaxDynSmem) continue;
+        int worst = -1;  // the instance with the largest resident state of the class
+        int64_t wr = -1;
+        for (int32_t b = 0; b < n; b++)
+          if (h->cls[b] == k) {
+            const int64_t r = res_floats(cfgs[b].M, cfgs[b].l, cfgs[b].Ks,
+                                         (cfgs[b].N + class_csize(k) - 1) / class_csize(k));
+            if (r > wr) { wr = r; worst = b; }
+          }
+        h->cls[worst] = k == 0 ? kNumClasses - 1 : k - 1;
+        h->descs[worst].nchunk = class_nchunk(cfgs[worst].N, cfgs[worst].K, class_csize(h->cls[worst]));
+        moved = true;
+      }
+      if (!moved) break;
+    }
+    {  // streamed class: staging when the double buffers fit, else global reads
+      LaunchClass &L = h->classes[kNumClasses - 1];
+      if (L.count > 0 && plan_kdims(L.kd, int64_t(1) << 40) != 0) { delete h; return HCRAN_EINVAL; }
+    }
+    // arenas (the chunk count of an instance depends on its class)
+    doff = foff = ioff = 0;
+    for (int32_t b = 0; b < n; b++) {
+      const hcran_config &c = cfgs[b];
+      InstDesc &d = h->descs[b];
       const DLayout dl = dlayout(c.M, c.N, c.K, c.Ks, c.l);
       const FLayout fl = flayout(c.M, c.N, c.K, c.l, d.nchunk);
       const ILayout il = ilayout(c.M, c.N, c.K, c.l);
       d.d_off = doff; doff += al4(dl.total);
       d.f_off = foff; foff += al4(fl.total);
       d.i_off = ioff; ioff += al4(il.total);
-      h->kd.Upmax = std::max(h->kd.Upmax, slot_stride(c.M, c.l));
-      h->kd.Mmax = std::max(h->kd.Mmax, d.M);
-      h->kd.NPmax = std::max(h->kd.NPmax, d.npair);
-      h->kd.NPPmax = std::max(h->kd.NPPmax, pair_stride(c.M, c.l));
-      h->kd.KSmax = std::max(h->kd.KSmax, d.Ks);
-      res_need = std::max(res_need, res_floats(c.M, c.l, c.Ks, c.N));
     }
-    if (plan_kdims(h->kd, res_need) != 0) { delete h; return HCRAN_EINVAL; }
     h->gain_elems = al4(h->gain_elems);
     h->dtot = doff; h->ftot = foff; h->itot = ioff;
     // constants image of the double arena
@@ -137,18 +183,25 @@ extern "C" int hcran_create(hcran_t *out, const hcran_config *cfgs, int32_t n,
       for (int k = 0; k < c.Ks; k++) db[dl.Psi + k] = min_rate(c.T_s[k], c.lambda_pps[k], c.zbar_bits, c.Bn_hz);
       for (int64_t t = 0; t < int64_t(c.M) * c.K; t++) db[dl.w + t] = c.w ? c.w[t] : 1.0;
     }
-    // longest-processing-time order: largest M*N*K first
+    // classes in launch order (largest clusters first); longest-processing-time
+    // order inside a class: largest M*N*K*l first
     h->order.resize(n);
     std::iota(h->order.begin(), h->order.end(), 0);
     std::stable_sort(h->order.begin(), h->order.end(), [&](int a, int b) {
+      if (h->cls[a] != h->cls[b]) return h->cls[a] < h->cls[b];
       const InstDesc &x = h->descs[a], &y = h->descs[b];
       return int64_t(x.N) * x.M * x.K * x.l > int64_t(y.N) * y.M * y.K * y.l;
     });
+    for (int k = 0, first = 0; k < kNumClasses; k++) {
+      h->classes[k].csize = class_csize(k);
+      h->classes[k].first = first;
+      first += h->classes[k].count;
+    }
     WsLayout &w = h->ws;
     uint64_t o = 0;
     w.descs = o; o = al256(o + sizeof(InstDesc) * n);
     w.order = o; o = al256(o + sizeof(int32_t) * n);
-    w.counter = o; o = al256(o + sizeof(int32_t));
+    w.counter = o; o = al256(o + sizeof(int32_t) * kNumClasses);
     w.outs = o; o = al256(o + sizeof(InstOut) * n);
     w.darena = o; o = al256(o + sizeof(double) * h->dtot);
     w.farena = o; o = al256(o + sizeof(float) * h->ftot);
@@ -213,12 +266,19 @@ static int do_solve(hcran_t h, const float *gains_dev, const hcran_tol *tol, voi
   t.tie_eps = (float)tol->tie_eps;
   t.q_init = tol->q_init;
   int launches = 0;
-  cudaError_t err = launch_solve(
-      reinterpret_cast<const InstDesc *>(ws + h->ws.descs), reinterpret_cast<const int *>(ws + h->ws.order),
-      h->n, gains_dev, reinterpret_cast<double *>(ws + h->ws.darena),
-      reinterpret_cast<float *>(ws + h->ws.farena), reinterpret_cast<int *>(ws + h->ws.iarena),
-      reinterpret_cast<InstOut *>(ws + h->ws.outs), t, h->kd, reinterpret_cast<int *>(ws + h->ws.counter),
-      static_cast<cudaStream_t>(stream), &launches);
+  cudaError_t err = cudaSuccess;
+  for (int k = 0; k < kNumClasses && err == cudaSuccess; k++) {
+    const LaunchClass &L = h->classes[k];
+    if (L.count == 0) continue;
+    int l = 0;
+    err = launch_solve(reinterpret_cast<const InstDesc *>(ws + h->ws.descs),
+                       reinterpret_cast<const int *>(ws + h->ws.order) + L.first, L.count, gains_dev,
+                       reinterpret_cast<double *>(ws + h->ws.darena), reinterpret_cast<float *>(ws + h->ws.farena),
+                       reinterpret_cast<int *>(ws + h->ws.iarena), reinterpret_cast<InstOut *>(ws + h->ws.outs),
+                       t, L.kd, L.csize, reinterpret_cast<int *>(ws + h->ws.counter) + k,
+                       static_cast<cudaStream_t>(stream), &l);
+    launches += l;
+  }
   h->last_ws = workspace_dev;
   h->last_stream = static_cast<cudaStream_t>(stream);
   h->last_launches = launches;
@@ -352,6 +412,13 @@ extern "C" int hcran_get_phase_cycles(hcran_t h, int64_t *cycles) {
 extern "C" int hcran_last_launch_count(hcran_t h, int32_t *launches) {
   if (!h || !launches) return HCRAN_EINVAL;
   *launches = h->last_launches;
+  return HCRAN_OK;
+}
+
+extern "C" int hcran_get_schedule(hcran_t h, int32_t *cluster_size) {
+  if (!h || !cluster_size) return HCRAN_EINVAL;
+  for (int32_t b = 0; b < h->n; b++)
+    cluster_size[b] = h->cls[b] < kNumClasses - 1 ? class_csize(h->cls[b]) : 0;
   return HCRAN_OK;
 }
 

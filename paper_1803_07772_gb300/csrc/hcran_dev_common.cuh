@@ -1,6 +1,7 @@
 // hcran_dev_common.cuh -- device-side context, shared-memory views, reductions
 // and the bulk-copy / mbarrier primitives used by the solver (internal).
 #pragma once
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -22,6 +23,8 @@ constexpr int kStatusTimeout = 16;   // per-instance status bit: a bounded wait 
 
 struct Ctx {
   int M, N, K, Ks, Ke, l, U, Up, NPp, npair, nchunk;
+  int crank, csize;  // rank of this CTA in the cluster that solves the instance, cluster size
+  int n0, n1;        // subcarriers [n0, n1) belong to this CTA
   const float *G;  // Gamma[n][m][k]
   const double *pmax, *eta, *mask, *Psi, *w;
   double *xi, *zeta, *zsic, *zsic_next;
@@ -44,6 +47,10 @@ struct Shared {
   int redi[kWarps];
   unsigned long long bar[kWarps][2];  // per-warp mbarriers of the two staging buffers
   long long cyc[8];  // SM clock cycles per phase of the current instance (thread 0)
+  double cxd;        // cluster reductions: this CTA's value, read by the peers
+  float cxf;
+  int cxi;
+  double vpart[kMaxM], vtot[kMaxM];  // per-RRH vectors summed over the cluster
   int inst;
   int abort;
   float min_margin;
@@ -250,6 +257,79 @@ __device__ inline int block_isum(int v, Shared &sh) {
   __syncthreads();
   return t;
 }
+
+// ------------------------------------------------------------------ cluster of CTAs
+//
+// An instance is solved by a cluster of csize CTAs (csize = 1: one CTA); CTA r
+// owns subcarriers [n0, n1).  Sums over subcarriers are formed per CTA, then
+// combined in rank order through distributed shared memory, so every CTA of
+// the cluster gets bit-identical totals and takes the same decisions.
+
+// barrier over the CTAs that solve the instance; orders their global and
+// shared memory accesses (release / acquire at cluster scope)
+__device__ __forceinline__ void inst_sync(const Ctx &c) {
+  if (c.csize > 1) cooperative_groups::this_cluster().sync();
+  else __syncthreads();
+}
+template <typename T>
+__device__ __forceinline__ T *peer(T *p, int rank) {
+  return cooperative_groups::this_cluster().map_shared_rank(p, rank);
+}
+
+__device__ inline double cl_sum(double v, Shared &sh, const Ctx &c) {
+  v = block_sum(v, sh);
+  if (c.csize == 1) return v;
+  if (threadIdx.x == 0) sh.cxd = v;
+  inst_sync(c);
+  double t = 0.0;
+  for (int r = 0; r < c.csize; r++) t += *peer(&sh.cxd, r);
+  inst_sync(c);
+  return t;
+}
+__device__ inline float cl_max(float v, Shared &sh, const Ctx &c) {
+  v = block_max(v, sh);
+  if (c.csize == 1) return v;
+  if (threadIdx.x == 0) sh.cxf = v;
+  inst_sync(c);
+  float t = *peer(&sh.cxf, 0);
+  for (int r = 1; r < c.csize; r++) t = fmaxf(t, *peer(&sh.cxf, r));
+  inst_sync(c);
+  return t;
+}
+__device__ inline float cl_min(float v, Shared &sh, const Ctx &c) {
+  v = block_min(v, sh);
+  if (c.csize == 1) return v;
+  if (threadIdx.x == 0) sh.cxf = v;
+  inst_sync(c);
+  float t = *peer(&sh.cxf, 0);
+  for (int r = 1; r < c.csize; r++) t = fminf(t, *peer(&sh.cxf, r));
+  inst_sync(c);
+  return t;
+}
+__device__ inline int cl_isum(int v, Shared &sh, const Ctx &c) {
+  v = block_isum(v, sh);
+  if (c.csize == 1) return v;
+  if (threadIdx.x == 0) sh.cxi = v;
+  inst_sync(c);
+  int t = 0;
+  for (int r = 0; r < c.csize; r++) t += *peer(&sh.cxi, r);
+  inst_sync(c);
+  return t;
+}
+// sh.vtot[i] = sum over the cluster of sh.vpart[i], i < n (each CTA has
+// filled its sh.vpart; the call synchronises before and after)
+__device__ inline void cl_vsum(Shared &sh, const Ctx &c, int n) {
+  inst_sync(c);
+  for (int i = threadIdx.x; i < n; i += kThreads) {
+    double t = 0.0;
+    for (int r = 0; r < c.csize; r++) t += c.csize == 1 ? sh.vpart[i] : peer(sh.vpart, r)[i];
+    sh.vtot[i] = t;
+  }
+  inst_sync(c);
+}
+// work items [0, count) shared out over the cluster: first index and stride
+__device__ __forceinline__ int cl_first(const Ctx &c) { return c.crank * kThreads + (int)threadIdx.x; }
+__device__ __forceinline__ int cl_stride(const Ctx &c) { return c.csize * kThreads; }
 
 // ------------------------------------------------------------------ model helpers
 

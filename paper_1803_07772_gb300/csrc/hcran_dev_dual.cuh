@@ -50,16 +50,16 @@ __device__ float sweep(const Ctx &c, Shared &sh, float *dyn, const KDims &kd, co
   }
   float dl = 0.f;
   int i = 0;
-  if (kd.staged && warp < c.N && lane == 0) {
-    issue_stage(c, sh, kd, wb.stage0, warp, 0, warp, zsrc);
+  if (kd.staged && c.n0 + warp < c.n1 && lane == 0) {
+    issue_stage(c, sh, kd, wb.stage0, warp, 0, c.n0 + warp, zsrc);
     pending |= 1u;
   }
-  for (int n = warp; n < c.N; n += kWarps, i++) {
+  for (int n = c.n0 + warp; n < c.n1; n += kWarps, i++) {
     SubView v;
     if (kd.staged) {
       const int b = i & 1;
       const int nn = n + kWarps;
-      if (nn < c.N) {
+      if (nn < c.n1) {
         __syncwarp();  // every lane is done reading buffer b^1 before the copy refills it
         if (lane == 0) issue_stage(c, sh, kd, b ? wb.stage0 : wb.stage1, warp, b ^ 1, nn, zsrc);
         pending |= 2u >> b;  // bit of buffer b^1
@@ -164,7 +164,7 @@ __device__ int dual_loop(const Ctx &c, Shared &sh, float *dyn, const KDims &kd, 
 
 // alpha/beta of the SCALE bound at the current point (gamma of the last link pass)
 __device__ void scale_update(const Ctx &c) {
-  for (int e = threadIdx.x; e < c.N * c.Up; e += kThreads) {
+  for (int e = c.n0 * c.Up + threadIdx.x; e < c.n1 * c.Up; e += kThreads) {
     if (c.S[e] < 0) continue;
     const float z = fmaxf(c.gam[e], kGammaFloor);
     const float a = z / (1.f + z);
@@ -177,15 +177,15 @@ __device__ void scale_update(const Ctx &c) {
 // exact R (elastic, weighted) and P of problem (eq7) from the last link pass
 __device__ void exact_R_P(const Ctx &c, Shared &sh, double &R, double &P) {
   double r = 0.0, tx = 0.0;
-  for (int e = threadIdx.x; e < c.N * c.Up; e += kThreads) {
+  for (int e = c.n0 * c.Up + threadIdx.x; e < c.n1 * c.Up; e += kThreads) {
     const int k = c.S[e];
     if (k < 0 || k >= c.Ke) continue;
     const int m = (e % c.Up) / c.l;
     r += (double)c.w[(size_t)m * c.K + k] * (double)(log1pf(c.gam[e]) / LN2F);
     tx += c.eta[m] * (double)c.p[e];
   }
-  R = block_sum(r, sh);
-  P = c.Pconst + block_sum(tx, sh);
+  R = cl_sum(r, sh, c);
+  P = c.Pconst + cl_sum(tx, sh, c);
 }
 
 // exact C12: scale an RRH's powers down when its total exceeds pmax
@@ -193,16 +193,21 @@ __device__ void project_power(const Ctx &c, Shared &sh) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int m = warp; m < c.M; m += kWarps) {
     double t = 0.0;
-    for (int n = lane; n < c.N; n += 32)
+    for (int n = c.n0 + lane; n < c.n1; n += 32)
       for (int s = 0; s < c.l; s++) {
         const int e = n * c.Up + m * c.l + s;
         if (c.S[e] >= 0) t += (double)c.p[e];
       }
     t = warp_sum(t);
-    if (lane == 0) sh.fac[m] = t > c.pmax[m] ? (float)(c.pmax[m] / t) : 1.f;
+    if (lane == 0) sh.vpart[m] = t;
+  }
+  cl_vsum(sh, c, c.M);
+  for (int m = threadIdx.x; m < c.M; m += kThreads) {
+    const double t = sh.vtot[m];
+    sh.fac[m] = t > c.pmax[m] ? (float)(c.pmax[m] / t) : 1.f;
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < c.N * c.Up; e += kThreads) {
+  for (int e = c.n0 * c.Up + threadIdx.x; e < c.n1 * c.Up; e += kThreads) {
     if (c.S[e] < 0) continue;
     const int m = (e % c.Up) / c.l;
     const float f = sh.fac[m];

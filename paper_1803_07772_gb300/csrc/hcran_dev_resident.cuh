@@ -40,8 +40,9 @@ struct RView {
 
 struct RScratch {
   float *xch0, *xch1;  // per-CTA partial sums, by iteration parity
+  float *xtot;         // their totals over the cluster
   double *xi, *zeta;
-  float *ipmax, *xscale, *psi;  // 1 / pmax_m, 1 / (ln2 mask_m), Psi_k
+  float *pmf, *xscale, *psi;  // pmax_m, 1 / (ln2 mask_m), Psi_k
 };
 
 __device__ __forceinline__ RScratch res_scratch(float *dyn, const KDims &kd) {
@@ -50,12 +51,13 @@ __device__ __forceinline__ RScratch res_scratch(float *dyn, const KDims &kd) {
   RScratch s;
   s.xch0 = b;
   s.xch1 = b + xf;
-  b += 2 * xf;
+  s.xtot = b + 2 * xf;
+  b += 3 * xf;
   s.xi = reinterpret_cast<double *>(b);
   b += 2 * al4(kd.Mmax);
   s.zeta = reinterpret_cast<double *>(b);
   b += 2 * al4(kd.KSmax > 0 ? kd.KSmax : 1);
-  s.ipmax = b;
+  s.pmf = b;
   b += al4(kd.Mmax);
   s.xscale = b;
   b += al4(kd.Mmax);
@@ -476,14 +478,14 @@ __device__ int dual_loop_res(const Ctx &c, Shared &sh, float *dyn, const KDims &
                              const Tol &tol, long long *cyc, unsigned &phase, unsigned &pending) {
   const int Vmax = tol.max_dual > 0 ? tol.max_dual : 1;
   const int M = c.M, Ks = c.Ks;
-  const RView r = res_view(dyn + dyn_head_floats(kd), c, c.N);
+  const RView r = res_view(dyn + dyn_head_floats(kd), c, c.n1 - c.n0);
   const RScratch x = res_scratch(dyn, kd);
   const long long t0 = clock64();
   const GIt gi = group_iter(M);
-  load_res(c, r, 0);
+  load_res(c, r, c.n0);
   for (int m = threadIdx.x; m < M; m += kThreads) {
     x.xi[m] = c.xi[m];
-    x.ipmax[m] = (float)(1.0 / c.pmax[m]);
+    x.pmf[m] = (float)c.pmax[m];
     x.xscale[m] = 1.f / (LN2F * sh.maskf[m]);
   }
   for (int k = threadIdx.x; k < Ks; k += kThreads) {
@@ -502,18 +504,37 @@ __device__ int dual_loop_res(const Ctx &c, Shared &sh, float *dyn, const KDims &
   int v = 0;
   for (;;) {
     const long long t1 = clock64();
+    // residual sums at p^v and max |p^v - p^{v-1}| / mask, over the cluster
     float *xv = (v & 1) ? x.xch1 : x.xch0;
+    const int nx = M + 2 * Ks;
     res_partials(c, sh, r, xv, dl);
     __syncthreads();
-    float d = sh.redf[0];
-    for (int i = 1; i < kWarps; i++) d = fmaxf(d, sh.redf[i]);
+    if (threadIdx.x == 0) {
+      float d = sh.redf[0];
+      for (int i = 1; i < kWarps; i++) d = fmaxf(d, sh.redf[i]);
+      xv[nx] = d;
+    }
+    const float *xt = xv;
+    if (c.csize > 1) {
+      // peers read this parity's vector before their next barrier; it is
+      // rewritten two iterations later, after that barrier
+      inst_sync(c);
+      for (int i = threadIdx.x; i <= nx; i += kThreads) {
+        float t = peer(xv, 0)[i];
+        for (int q = 1; q < c.csize; q++) t = i < nx ? t + peer(xv, q)[i] : fmaxf(t, peer(xv, q)[i]);
+        x.xtot[i] = t;
+      }
+      xt = x.xtot;
+    }
+    __syncthreads();
+    const float d = xt[nx];
     if ((v > 0 && d < (float)tol.tol_dual) || v >= Vmax) break;
     const float delta = rsqrtf((float)v + 1.f);
     for (int t = threadIdx.x; t < M + Ks; t += kThreads) {
       if (t < M) {
         const int m = t;
-        const float ip = x.ipmax[m];
-        const float step = delta * ((xv[m] * ip - 1.f) * x.xscale[m]);
+        const float pm = x.pmf[m];
+        const float step = delta * ((xt[m] - pm) / pm) * x.xscale[m];
         double xm = x.xi[m];
         if (xm != 0.0 || step > 0.f) {
           xm += (double)step;
@@ -523,7 +544,7 @@ __device__ int dual_loop_res(const Ctx &c, Shared &sh, float *dyn, const KDims &
         sh.xif[m] = (float)xm;
       } else {
         const int ks = t - M;
-        const float rr = xv[M + ks], as = xv[M + Ks + ks];
+        const float rr = xt[M + ks], as = xt[M + Ks + ks];
         const float e = fminf(fmaxf((x.psi[ks] - rr) / fmaxf(as, (float)kZetaAsumMin), -1.f), 1.f);
         const double z = fmin(fmax(x.zeta[ks] * (double)exp2f(e), kZetaMin), kZetaMax);
         x.zeta[ks] = z;
@@ -545,9 +566,11 @@ __device__ int dual_loop_res(const Ctx &c, Shared &sh, float *dyn, const KDims &
       cyc[3] += t3 - t2;
     }
   }
-  store_res(c, r, 0, zc);
-  for (int m = threadIdx.x; m < M; m += kThreads) c.xi[m] = x.xi[m];
-  for (int k = threadIdx.x; k < Ks; k += kThreads) c.zeta[k] = x.zeta[k];
+  store_res(c, r, c.n0, zc);
+  if (c.crank == 0) {
+    for (int m = threadIdx.x; m < M; m += kThreads) c.xi[m] = x.xi[m];
+    for (int k = threadIdx.x; k < Ks; k += kThreads) c.zeta[k] = x.zeta[k];
+  }
   // gamma, pi, X, totals and SIC sums at the final point for the later phases
   link_all<kLinkOnly>(c, sh, dyn, kd, szeta, 0.f, phase, pending);
   return v;

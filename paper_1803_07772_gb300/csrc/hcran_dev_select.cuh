@@ -61,20 +61,24 @@ __device__ float cand_utility(const Ctx &c, const Shared &sh, const float *szeta
 // repack the gains of the selected users: slab[n][j][u] = Gamma_{j, S[n][u]}^{(n)}
 // for the RRHs j other than the slot's own, gown/ginv = the serving gain and its reciprocal
 __device__ void build_slab(const Ctx &c) {
-  for (int t = threadIdx.x; t < c.K * c.N; t += kThreads) c.uslot[t] = -1;
+  const int Nc = c.n1 - c.n0;
+  for (int t = threadIdx.x; t < c.K * Nc; t += kThreads) {
+    const int k = t / Nc;
+    c.uslot[(size_t)k * c.N + c.n0 + (t - k * Nc)] = -1;
+  }
   __syncthreads();
-  for (int e = threadIdx.x; e < c.N * c.Up; e += kThreads) {
+  for (int e = c.n0 * c.Up + threadIdx.x; e < c.n1 * c.Up; e += kThreads) {
     const int k = c.S[e];
     if (k >= 0) c.uslot[(size_t)k * c.N + e / c.Up] = e % c.Up;
   }
   const int MU = c.M * c.Up;
-  for (int t = threadIdx.x; t < c.N * MU; t += kThreads) {
+  for (int t = c.n0 * MU + threadIdx.x; t < c.n1 * MU; t += kThreads) {
     const int n = t / MU, r = t - n * MU, j = r / c.Up, u = r - j * c.Up;
     const int k = u < c.U ? c.S[n * c.Up + u] : -1;
     const bool own = u < c.U && j == u / c.l;
     c.slab[t] = (k >= 0 && !own) ? gain(c, n, j, k) : 0.f;
   }
-  for (int e = threadIdx.x; e < c.N * c.Up; e += kThreads) {
+  for (int e = c.n0 * c.Up + threadIdx.x; e < c.n1 * c.Up; e += kThreads) {
     const int k = c.S[e], u = e % c.Up;
     const float g = k >= 0 ? gain(c, e / c.Up, u / c.l, k) : 0.f;
     c.gown[e] = g;
@@ -194,27 +198,29 @@ __device__ int selection(const Ctx &c, Shared &sh, float *dyn, const KDims &kd, 
   link_all<kLinkOnly>(c, sh, dyn, kd, szeta, 0.f, phase, pending);  // prices, totals, SIC sums
   float mm = 1.f;
   int nt = 0;
-  // (A) per-chunk sums over n of the candidate utilities
-  const int nch = c.nchunk;
+  // (A) per-chunk sums over n of the candidate utilities; the chunks split this
+  // CTA's subcarriers, chunk ch of CTA r is global chunk r * nch + ch
+  const int nch = c.nchunk / c.csize, Nc = c.n1 - c.n0;
   for (int t = threadIdx.x; t < nch * c.K; t += kThreads) {
     const int ch = t / c.K, k = t - ch * c.K;
-    const int n0 = (int)((int64_t)c.N * ch / nch), n1 = (int)((int64_t)c.N * (ch + 1) / nch);
-    float *up = c.Upart + (size_t)ch * c.M * c.K + k;
+    const int n0 = c.n0 + (int)((int64_t)Nc * ch / nch), n1 = c.n0 + (int)((int64_t)Nc * (ch + 1) / nch);
+    float *up = c.Upart + (size_t)(c.crank * nch + ch) * c.M * c.K + k;
     for (int m = 0; m < c.M; m++) {
       float acc = 0.f;
       for (int n = n0; n < n1; n++) acc += cand_utility(c, sh, szeta, n, m, k, nullptr, nullptr, nullptr);
       up[(size_t)m * c.K] = acc;
     }
   }
-  __syncthreads();
+  inst_sync(c);
   // (B) A_k = argmax_m sum_n u, lowest m on equal sums, -1 when all zero
+  // (users shared out over the cluster)
   int ch_local = 0;
-  for (int k = threadIdx.x; k < c.K; k += kThreads) {
+  for (int k = cl_first(c); k < c.K; k += cl_stride(c)) {
     int best = -1;
     float b1 = 0.f, b2 = 0.f;
     for (int m = 0; m < c.M; m++) {
       float U = 0.f;
-      for (int ch = 0; ch < nch; ch++) U += c.Upart[((size_t)ch * c.M + m) * c.K + k];
+      for (int ch = 0; ch < nch * c.csize; ch++) U += c.Upart[((size_t)ch * c.M + m) * c.K + k];
       if (U > b1) {
         b2 = b1;
         b1 = U;
@@ -227,9 +233,9 @@ __device__ int selection(const Ctx &c, Shared &sh, float *dyn, const KDims &kd, 
     c.Anew[k] = best;
     if (best != c.A[k]) ch_local = 1;
   }
-  __syncthreads();
+  inst_sync(c);
   // (C) the candidate of every (n, k) on its chosen RRH
-  for (int t = threadIdx.x; t < c.N * c.K; t += kThreads) {
+  for (int t = c.n0 * c.K + threadIdx.x; t < c.n1 * c.K; t += kThreads) {
     const int n = t / c.K, k = t - n * c.K;
     const int m = c.Anew[k];
     if (m < 0) {
@@ -247,16 +253,16 @@ __device__ int selection(const Ctx &c, Shared &sh, float *dyn, const KDims &kd, 
   }
   __syncthreads();
   // (D) admission per (n, m)
-  for (int nm = threadIdx.x; nm < c.N * c.M; nm += kThreads)
+  for (int nm = c.n0 * c.M + threadIdx.x; nm < c.n1 * c.M; nm += kThreads)
     if (admit(c, nm / c.M, nm % c.M, tie_eps, mm, nt)) ch_local = 1;
-  __syncthreads();
-  for (int k = threadIdx.x; k < c.K; k += kThreads) c.A[k] = c.Anew[k];
+  inst_sync(c);  // every CTA has read A
+  for (int k = cl_first(c); k < c.K; k += cl_stride(c)) c.A[k] = c.Anew[k];
   __syncthreads();
   build_slab(c);
-  // fold decision margins and the change flag
-  const float bm = block_min(mm, sh);
-  const int bt = block_isum(nt, sh);
-  const int anych = block_isum(ch_local, sh);
+  // fold decision margins and the change flag (the reductions synchronise the cluster)
+  const float bm = cl_min(mm, sh, c);
+  const int bt = cl_isum(nt, sh, c);
+  const int anych = cl_isum(ch_local, sh, c);
   if (threadIdx.x == 0) {
     sh.min_margin = fminf(sh.min_margin, bm);
     sh.n_ties += bt;
@@ -269,14 +275,14 @@ __device__ int selection(const Ctx &c, Shared &sh, float *dyn, const KDims &kd, 
 // subcarrier (already in SIC order), p = mask / l; xi' = 0, zeta' = 1.
 __device__ void initial_state(const Ctx &c, float *szeta) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int e = threadIdx.x; e < c.N * c.Up; e += kThreads) {
+  for (int e = c.n0 * c.Up + threadIdx.x; e < c.n1 * c.Up; e += kThreads) {
     c.S[e] = -1;
     c.p[e] = 0.f;
     c.plin[e] = 0.f;
     c.alpha[e] = 1.f;
     c.beta[e] = 0.f;
   }
-  for (int k = threadIdx.x; k < c.K; k += kThreads) {
+  for (int k = cl_first(c); k < c.K; k += cl_stride(c)) {
     int best = 0;
     float bv = -1.f;
     for (int m = 0; m < c.M; m++) {
@@ -289,8 +295,8 @@ __device__ void initial_state(const Ctx &c, float *szeta) {
     }
     c.A[k] = best;
   }
-  __syncthreads();
-  for (int nm = warp; nm < c.N * c.M; nm += kWarps) {
+  inst_sync(c);
+  for (int nm = c.n0 * c.M + warp; nm < c.n1 * c.M; nm += kWarps) {
     const int n = nm / c.M, m = nm - n * c.M;
     float pg = INFINITY;
     int pk = -1;
@@ -326,12 +332,12 @@ __device__ void initial_state(const Ctx &c, float *szeta) {
       pk = bk;
     }
   }
-  for (int m = threadIdx.x; m < c.M; m += kThreads) c.xi[m] = 0.0;
-  for (int k = threadIdx.x; k < c.Ks; k += kThreads) {
-    c.zeta[k] = 1.0;
-    szeta[k] = 1.f;
+  if (c.crank == 0) {
+    for (int m = threadIdx.x; m < c.M; m += kThreads) c.xi[m] = 0.0;
+    for (int k = threadIdx.x; k < c.Ks; k += kThreads) c.zeta[k] = 1.0;
   }
-  for (int t = threadIdx.x; t < c.N * c.NPp; t += kThreads) {
+  for (int k = threadIdx.x; k < c.Ks; k += kThreads) szeta[k] = 1.f;
+  for (int t = c.n0 * c.NPp + threadIdx.x; t < c.n1 * c.NPp; t += kThreads) {
     c.zsic[t] = 0.0;
     c.zsic_next[t] = 0.0;
   }

@@ -49,7 +49,7 @@ __device__ void solve_instance(const Ctx &c, Shared &sh, float *dyn, const KDims
     sh.pio_j[threadIdx.x] = (unsigned char)(threadIdx.x % c.M);
     sh.pio_ch[threadIdx.x] = (unsigned char)(threadIdx.x / c.M);
   }
-  for (int t = threadIdx.x; t < c.M * c.K; t += kThreads) c.wf[t] = (float)c.w[t];
+  for (int t = cl_first(c); t < c.M * c.K; t += cl_stride(c)) c.wf[t] = (float)c.w[t];
   if (threadIdx.x == 0) {
     for (int i = 0; i < 8; i++) sh.cyc[i] = 0;
     sh.min_margin = 1.f;
@@ -78,7 +78,7 @@ __device__ void solve_instance(const Ctx &c, Shared &sh, float *dyn, const KDims
     if (threadIdx.x == 0) cyc[0] += clock64() - ta;
     // Algorithm 1 at E^i = q (alpha = 1, beta = 0 written by the selection)
     for (int s = 0; s < Smax && !sh.abort; s++) {
-      for (int e = threadIdx.x; e < c.N * c.Up; e += kThreads) {
+      for (int e = c.n0 * c.Up + threadIdx.x; e < c.n1 * c.Up; e += kThreads) {
         c.pstart[e] = c.p[e];
         c.plin[e] = c.p[e];
       }
@@ -89,9 +89,9 @@ __device__ void solve_instance(const Ctx &c, Shared &sh, float *dyn, const KDims
       scale_update(c);
       it_s++;
       float dm = 0.f;
-      for (int e = threadIdx.x; e < c.N * c.Up; e += kThreads)
+      for (int e = c.n0 * c.Up + threadIdx.x; e < c.n1 * c.Up; e += kThreads)
         if (c.S[e] >= 0) dm = fmaxf(dm, fabsf(c.p[e] - c.pstart[e]) / sh.maskf[(e % c.Up) / c.l]);
-      dm = block_max(dm, sh);
+      dm = cl_max(dm, sh, c);
       if (threadIdx.x == 0) cyc[4] += clock64() - t5;
       if (dm < (float)tol.tol_scale) break;
     }
@@ -112,34 +112,43 @@ __device__ void solve_instance(const Ctx &c, Shared &sh, float *dyn, const KDims
       break;
     }
   }
-  // slacks (exact rates from the last link pass)
+  // slacks (exact rates from the last link pass), summed over the cluster
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float smin = INFINITY;
   for (int m = warp; m < c.M; m += kWarps) {
     double t = 0.0;
-    for (int n = lane; n < c.N; n += 32) t += (double)c.Ptot[n * c.M + m];
+    for (int n = c.n0 + lane; n < c.n1; n += 32) t += (double)c.Ptot[n * c.M + m];
     t = warp_sum(t);
-    smin = fminf(smin, (float)((c.pmax[m] - t) / c.pmax[m]));
+    if (lane == 0) sh.vpart[m] = t;
   }
+  cl_vsum(sh, c, c.M);
+  float smin = INFINITY;
+  for (int m = threadIdx.x; m < c.M; m += kThreads)
+    smin = fminf(smin, (float)((c.pmax[m] - sh.vtot[m]) / c.pmax[m]));
   const float slack_power = block_min(smin, sh);
   float rmin = INFINITY;
-  for (int ks = warp; ks < c.Ks; ks += kWarps) {
-    const int k = c.Ke + ks;
-    const int a = c.A[k];
-    float r = 0.f;
-    if (a >= 0) {
-      const float wk = c.wf[(size_t)a * c.K + k];
-      for (int n = lane; n < c.N; n += 32) {
-        const int u = c.uslot[(size_t)k * c.N + n];
-        if (u >= 0) r += wk * log1pf(c.gam[n * c.Up + u]) / LN2F;
+  for (int base = 0; base < c.Ks; base += kMaxM) {  // streaming users in groups of kMaxM
+    const int cnt = c.Ks - base < kMaxM ? c.Ks - base : kMaxM;
+    for (int i = warp; i < cnt; i += kWarps) {
+      const int k = c.Ke + base + i;
+      const int a = c.A[k];
+      float r = 0.f;
+      if (a >= 0) {
+        const float wk = c.wf[(size_t)a * c.K + k];
+        for (int n = c.n0 + lane; n < c.n1; n += 32) {
+          const int u = c.uslot[(size_t)k * c.N + n];
+          if (u >= 0) r += wk * log1pf(c.gam[n * c.Up + u]) / LN2F;
+        }
       }
+      r = warp_sum(r);
+      if (lane == 0) sh.vpart[i] = r;
     }
-    r = warp_sum(r);
-    rmin = fminf(rmin, (float)((r - c.Psi[ks]) / c.Psi[ks]));
+    cl_vsum(sh, c, cnt);
+    for (int i = threadIdx.x; i < cnt; i += kThreads)
+      rmin = fminf(rmin, (float)((sh.vtot[i] - c.Psi[base + i]) / c.Psi[base + i]));
   }
   const float slack_rate = block_min(rmin, sh);
   float smax = -INFINITY;
-  for (int nm = threadIdx.x; nm < c.N * c.M; nm += kThreads) {
+  for (int nm = c.n0 * c.M + threadIdx.x; nm < c.n1 * c.M; nm += kThreads) {
     const int n = nm / c.M, m = nm - n * c.M;
     const int base = n * c.Up + m * c.l;
     for (int a = 0; a < c.l; a++) {
@@ -152,8 +161,8 @@ __device__ void solve_instance(const Ctx &c, Shared &sh, float *dyn, const KDims
       }
     }
   }
-  const float slack_sic = block_max(smax, sh);
-  if (threadIdx.x == 0) {
+  const float slack_sic = cl_max(smax, sh, c);
+  if (threadIdx.x == 0 && c.crank == 0) {
     if (c.Ks > 0 && slack_rate < -1e-3f) status |= 2;
     if (sh.abort) status |= kStatusTimeout;
     out->ee = R / P;
@@ -212,6 +221,10 @@ __global__ void __launch_bounds__(kThreads, 1)
   __shared__ Ctx sc;
   extern __shared__ __align__(16) float dyn[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // a launch with clusters solves each instance on one cluster; CTA r of the
+  // cluster owns a contiguous share of the subcarriers
+  const int csize = (int)cooperative_groups::this_cluster().num_blocks();
+  const int crank = (int)cooperative_groups::this_cluster().block_rank();
   if (lane == 0) {
     mbar_init(&sh.bar[warp][0], 1);
     mbar_init(&sh.bar[warp][1], 1);
@@ -220,15 +233,24 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   unsigned phase = 0, pending = 0;  // per-warp mbarrier parity and copies in flight
   for (;;) {
-    if (threadIdx.x == 0) sh.inst = atomicAdd(counter, 1);
-    __syncthreads();
-    const int w = sh.inst;
-    __syncthreads();
+    if (crank == 0 && threadIdx.x == 0) sh.inst = atomicAdd(counter, 1);
+    if (csize > 1) cooperative_groups::this_cluster().sync();
+    else __syncthreads();
+    const int w = csize > 1 ? *peer(&sh.inst, 0) : sh.inst;
+    // nobody reads the leader's slot after this barrier until it is rewritten
+    if (csize > 1) cooperative_groups::this_cluster().sync();
+    else __syncthreads();
     if (w >= n_inst) break;
     const int b = order[w];
     // the instance context lives in shared memory: every field read is a
     // shared load instead of a local-memory one
-    if (threadIdx.x == 0) bind(sc, descs[b], gains, darena, farena, iarena);
+    if (threadIdx.x == 0) {
+      bind(sc, descs[b], gains, darena, farena, iarena);
+      sc.csize = csize;
+      sc.crank = crank;
+      sc.n0 = (int)((int64_t)sc.N * crank / csize);
+      sc.n1 = (int)((int64_t)sc.N * (crank + 1) / csize);
+    }
     __syncthreads();
     solve_instance(sc, sh, dyn, kd, tol, outs + b, phase, pending);
   }
@@ -239,9 +261,14 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 }
 
+// One persistent launch over n_inst instances (indices order[0..n_inst)),
+// each solved by a cluster of csize CTAs (csize = 1: one CTA).  The grid is
+// as many clusters as can be resident at once, capped at n_inst.
 cudaError_t launch_solve(const InstDesc *descs, const int *order, int n_inst, const float *gains,
                          double *darena, float *farena, int *iarena, InstOut *outs, const Tol &tol,
-                         const KDims &kd, int *counter, cudaStream_t stream, int *launches) {
+                         const KDims &kd, int csize, int *counter, cudaStream_t stream, int *launches) {
+  *launches = 0;
+  if (n_inst <= 0) return cudaSuccess;
   int dev = 0, sms = 0, per_sm = 0;
   cudaError_t err = cudaGetDevice(&dev);
   if (err != cudaSuccess) return err;
@@ -250,16 +277,35 @@ cudaError_t launch_solve(const InstDesc *descs, const int *order, int n_inst, co
   const int smem = (int)dyn_smem_bytes(kd);
   err = cudaFuncSetAttribute(solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (err != cudaSuccess) return err;
-  err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, solve_kernel, kThreads, smem);
-  if (err != cudaSuccess) return err;
-  if (per_sm < 1) per_sm = 1;
-  int grid = sms * per_sm;
-  if (grid > n_inst) grid = n_inst;
-  if (grid < 1) grid = 1;
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  cfg.blockDim = dim3(kThreads, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = stream;
+  int clusters = 0;
+  if (csize > 1) {
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = csize;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cfg.gridDim = dim3(csize * sms, 1, 1);
+    err = cudaOccupancyMaxActiveClusters(&clusters, solve_kernel, &cfg);
+    if (err != cudaSuccess) return err;
+    if (clusters < 1) return cudaErrorInvalidConfiguration;
+  } else {
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, solve_kernel, kThreads, smem);
+    if (err != cudaSuccess) return err;
+    clusters = sms * (per_sm > 0 ? per_sm : 1);
+  }
+  if (clusters > n_inst) clusters = n_inst;
+  cfg.gridDim = dim3(clusters * csize, 1, 1);
   err = cudaMemsetAsync(counter, 0, sizeof(int), stream);
   if (err != cudaSuccess) return err;
-  solve_kernel<<<grid, kThreads, smem, stream>>>(descs, order, n_inst, gains, darena, farena, iarena,
-                                                  outs, tol, kd, counter);
+  err = cudaLaunchKernelEx(&cfg, solve_kernel, descs, order, n_inst, gains, darena, farena, iarena, outs,
+                           tol, kd, counter);
+  if (err != cudaSuccess) return err;
   *launches = 1;
   return cudaGetLastError();
 }

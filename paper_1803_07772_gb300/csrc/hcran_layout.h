@@ -183,15 +183,16 @@ HCRAN_HD int64_t res_floats(int M, int l, int Ks, int Nc) {
          4 * al4(int64_t(Nc) * M) + 4 * al4(int64_t(Nc) * Mi) + al4(int64_t(Nc) * NW) +
          2 * al4(int64_t(Nc) * Ks);
 }
-// resident scratch: cluster exchange vectors (two parities), the FP64
+// resident scratch: cluster exchange vectors (two parities) and their
+// totals over the cluster, the FP64
 // multipliers xi', zeta' of the CTA, and the constants of their steps
-// (1 / pmax_m, 1 / (ln2 mask_m), Psi_k) in FP32
+// (pmax_m, 1 / (ln2 mask_m), Psi_k) in FP32
 HCRAN_HD int res_xch_floats(const KDims &k) {
   return int(al4(k.Mmax + 2 * (k.KSmax > 0 ? k.KSmax : 1) + 2));
 }
 HCRAN_HD int res_scratch_floats(const KDims &k) {
   const int m4 = int(al4(k.Mmax)), s4 = int(al4(k.KSmax > 0 ? k.KSmax : 1));
-  return 2 * res_xch_floats(k) + 2 * m4 + 2 * s4 + 2 * m4 + s4;  // + 1/pmax, xi step scale, Psi
+  return 3 * res_xch_floats(k) + 2 * m4 + 2 * s4 + 2 * m4 + s4;  // + pmax, xi step scale, Psi
 }
 // Dynamic shared memory: streaming multipliers zeta' (FP32), the resident
 // scratch, then one region that holds either the per-warp buffers of the
@@ -221,6 +222,55 @@ inline int plan_kdims(KDims &k, int64_t res_need) {
   if (dyn_smem_bytes(k) <= kMaxDynSmem) return 0;
   k.staged = 0;
   return dyn_smem_bytes(k) <= kMaxDynSmem ? 0 : 1;
+}
+
+// Launch dimensions for one instance of shape (M, l, Ks, N) solved with the
+// resident dual loop by clusters of C CTAs (each CTA holds ceil(N / C)
+// subcarriers).
+inline KDims resident_kdims(int M, int l, int Ks, int N, int C) {
+  KDims k;
+  k.Upmax = slot_stride(M, l);
+  k.Mmax = M;
+  k.NPmax = l * (l - 1) / 2;
+  k.NPPmax = pair_stride(M, l);
+  k.KSmax = Ks;
+  k.staged = 0;
+  k.resident = 1;
+  const int64_t r = res_floats(M, l, Ks, (N + C - 1) / C);
+  k.res_floats = int(r < (int64_t(1) << 30) ? r : (int64_t(1) << 30));
+  return k;
+}
+// dimensions of a launch that holds the instances of a and of b
+inline void kdims_merge(KDims &a, const KDims &b) {
+  a.Upmax = a.Upmax > b.Upmax ? a.Upmax : b.Upmax;
+  a.Mmax = a.Mmax > b.Mmax ? a.Mmax : b.Mmax;
+  a.NPmax = a.NPmax > b.NPmax ? a.NPmax : b.NPmax;
+  a.NPPmax = a.NPPmax > b.NPPmax ? a.NPPmax : b.NPPmax;
+  a.KSmax = a.KSmax > b.KSmax ? a.KSmax : b.KSmax;
+  a.res_floats = a.res_floats > b.res_floats ? a.res_floats : b.res_floats;
+}
+// Cluster sizes, largest first; launch class kNumClasses - 1 is the streamed
+// schedule (one CTA, subcarrier state staged from global memory) for
+// instances whose resident state does not fit even the largest cluster.
+constexpr int kNumClasses = 5;
+HCRAN_HD int class_csize(int cls) { return cls < 4 ? 8 >> cls : 1; }
+// margin kept free for the per-launch maxima of the other instances of a class
+constexpr int kClassMargin = 4096;
+// launch class of one instance: the smallest cluster whose resident state fits
+inline int pick_class(int M, int l, int Ks, int N) {
+  for (int cls = 3; cls >= 0; cls--) {
+    const int C = class_csize(cls);
+    if (C > N) break;
+    if (dyn_smem_bytes(resident_kdims(M, l, Ks, N, C)) <= kMaxDynSmem - kClassMargin) return cls;
+  }
+  return kNumClasses - 1;
+}
+// candidate-utility chunks of an instance solved by clusters of C CTAs: a
+// multiple of C, so that every CTA sums chunks of its own subcarriers
+inline int class_nchunk(int N, int K, int C) {
+  int per = nchunk_for(N, K) / C;
+  if (per < 1) per = 1;
+  return per * C;
 }
 
 struct Tol {

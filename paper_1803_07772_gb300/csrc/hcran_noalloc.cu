@@ -22,7 +22,7 @@
 namespace hcran {
 cudaError_t launch_solve(const InstDesc *descs, const int *order, int n_inst, const float *gains,
                          double *darena, float *farena, int *iarena, InstOut *outs, const Tol &tol,
-                         const KDims &kd, int *counter, cudaStream_t stream, int *launches);
+                         const KDims &kd, int csize, int *counter, cudaStream_t stream, int *launches);
 }
 
 using namespace hcran;
@@ -43,6 +43,7 @@ static void *g_scratch_dev[kMaxDevices];
 struct Plan {
   InstDesc d;
   KDims kd;
+  int csize;
   int32_t order;
   uint64_t o_desc, o_order, o_counter, o_out, o_darena, o_farena, o_iarena, o_tmp, total;
 };
@@ -78,7 +79,9 @@ int plan(const hcran_config &c, Plan &p) {
   d.U = c.M * c.l;
   d.L = c.N * d.U;
   d.npair = c.l * (c.l - 1) / 2;
-  d.nchunk = nchunk_for(c.N, c.K);
+  const int cls = pick_class(c.M, c.l, c.Ks, c.N);
+  p.csize = class_csize(cls);
+  d.nchunk = class_nchunk(c.N, c.K, p.csize);
   d.g_off = 0;
   d.sigma = c.N0_w_per_hz * c.Bn_hz;
   double pc = 0.0;
@@ -87,12 +90,16 @@ int plan(const hcran_config &c, Plan &p) {
   const DLayout dl = dlayout(c.M, c.N, c.K, c.Ks, c.l);
   const FLayout fl = flayout(c.M, c.N, c.K, c.l, d.nchunk);
   const ILayout il = ilayout(c.M, c.N, c.K, c.l);
-  p.kd.Upmax = slot_stride(c.M, c.l);
-  p.kd.Mmax = c.M;
-  p.kd.NPmax = d.npair;
-  p.kd.NPPmax = pair_stride(c.M, c.l);
-  p.kd.KSmax = c.Ks;
-  if (plan_kdims(p.kd, res_floats(c.M, c.l, c.Ks, c.N)) != 0) return HCRAN_EINVAL;
+  if (cls < kNumClasses - 1) {
+    p.kd = resident_kdims(c.M, c.l, c.Ks, c.N, p.csize);
+  } else {
+    p.kd.Upmax = slot_stride(c.M, c.l);
+    p.kd.Mmax = c.M;
+    p.kd.NPmax = d.npair;
+    p.kd.NPPmax = pair_stride(c.M, c.l);
+    p.kd.KSmax = c.Ks;
+    if (plan_kdims(p.kd, int64_t(1) << 40) != 0) return HCRAN_EINVAL;
+  }
   uint64_t o = 0;
   p.o_desc = o; o = al256(o + sizeof(InstDesc));
   p.o_order = o; o = al256(o + sizeof(int32_t));
@@ -195,7 +202,7 @@ extern "C" int hcran_solve_noalloc(const hcran_config *cfg, const float *gains_d
   if (launch_solve(reinterpret_cast<const InstDesc *>(ws + p.o_desc),
                    reinterpret_cast<const int *>(ws + p.o_order), 1, gains_dev, db,
                    reinterpret_cast<float *>(ws + p.o_farena), reinterpret_cast<int *>(ws + p.o_iarena),
-                   reinterpret_cast<InstOut *>(ws + p.o_out), t, p.kd,
+                   reinterpret_cast<InstOut *>(ws + p.o_out), t, p.kd, p.csize,
                    reinterpret_cast<int *>(ws + p.o_counter), st, &launches) != cudaSuccess)
     return HCRAN_ECUDA;
   if (cudaStreamSynchronize(st) != cudaSuccess) return HCRAN_ECUDA;

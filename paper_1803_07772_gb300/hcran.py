@@ -59,7 +59,7 @@ class Result(C.Structure):
 EXPORTS = ["hcran_create", "hcran_workspace_size", "hcran_gain_elems", "hcran_prepare",
            "hcran_solve", "hcran_solve_host", "hcran_get", "hcran_get_summary",
            "hcran_get_phase_cycles", "hcran_last_launch_count", "hcran_destroy",
-           "hcran_solve_noalloc"]
+           "hcran_solve_noalloc", "hcran_get_schedule"]
 
 
 def load(build_if_missing: bool = True):
@@ -179,6 +179,12 @@ class Solver:
         v = C.c_int32()
         _check("hcran_last_launch_count", self.lib.hcran_last_launch_count(self.h, C.byref(v)))
         return v.value
+
+    def schedule(self) -> np.ndarray:
+        """Cluster size per instance (0: one CTA streaming from global memory)."""
+        out = np.zeros(len(self.instances), np.int32)
+        _check("hcran_get_schedule", self.lib.hcran_get_schedule(self.h, out.ctypes.data_as(_ip)))
+        return out
 
     def get(self, i: int) -> dict:
         inst = self.instances[i]

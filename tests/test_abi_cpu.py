@@ -110,3 +110,39 @@ def test_null_arguments_rejected():
     assert lib.hcran_workspace_size(None, None) == 1
     assert lib.hcran_solve(None, None, None, None, None) == 1
     assert lib.hcran_get(None, 0, None) == 1
+
+
+def _res_bytes(M, l, Ks, Nc):
+    """Resident dual-loop footprint of Nc subcarriers, restated from the
+    layout the schedule documents (slab rows padded to an odd number of
+    float4, ten slot arrays, four per-RRH arrays, four SIC arrays, the
+    nonzero masks and two streaming arrays)."""
+    al4 = lambda x: (x + 3) & ~3
+    Up = al4(M * l)
+    Rs = Up if (Up // 4) % 2 == 1 else Up + 4
+    Mi = M * (l * (l - 1) // 2)
+    return 4 * (Nc * M * Rs + 10 * Nc * Up + 4 * al4(Nc * M) + 4 * al4(Nc * Mi)
+                + al4(Nc * ((Mi + 31) // 32)) + 2 * al4(Nc * Ks))
+
+
+def test_schedule_picks_smallest_cluster_that_holds_the_state():
+    lib = hcran.load()
+    insts = make_workload("batch-4096-uneven", count=64) + make_workload("large-33x1024x512", count=1)
+    made = [_cfg(i) for i in insts]
+    arr = (hcran.Config * len(made))(*[m[0] for m in made])
+    h = C.c_void_p()
+    assert lib.hcran_create(C.byref(h), arr, len(made), None) == 0
+    cs = np.zeros(len(insts), np.int32)
+    assert lib.hcran_get_schedule(h, cs.ctypes.data_as(hcran._ip)) == 0
+    assert lib.hcran_get_schedule(h, None) == 1
+    lib.hcran_destroy(h)
+    assert set(cs.tolist()) <= {0, 1, 2, 4, 8}
+    assert cs[-1] == 0  # 33 x 1024 x 512: streamed from global memory
+    budget = 216 * 1024
+    for inst, c in zip(insts[:-1], cs[:-1]):
+        assert c > 0
+        need = _res_bytes(inst.M, inst.l, inst.Ks, -(-inst.N // c))
+        assert need < budget, (inst.M, inst.N, c, need)
+        if c > 1:  # the next smaller cluster would not hold the state
+            smaller = _res_bytes(inst.M, inst.l, inst.Ks, -(-inst.N // (c // 2)))
+            assert smaller > budget - 8 * 1024, (inst.M, inst.N, c, smaller)
