@@ -18,8 +18,13 @@ constexpr float kGammaFloor = 1e-12f;
 constexpr float kInvLn2 = 1.44269504f;
 constexpr double kZetaAsumMin = 0.05;
 constexpr double kZetaMin = 1e-6, kZetaMax = 1e6;
+constexpr float kLog2ZetaMin = -19.9315686f, kLog2ZetaMax = 19.9315686f;  // log2 of the bounds
 constexpr int kSpinLimit = 1 << 22;  // bound on every mbarrier wait
 constexpr int kStatusTimeout = 16;   // per-instance status bit: a bounded wait gave up
+
+// dynamic shared memory of the solver kernel (one declaration for every
+// device function, so that pointers into it stay in the shared state space)
+extern __shared__ __align__(16) float hcran_dyn[];
 
 struct Ctx {
   int M, N, K, Ks, Ke, l, U, Up, NPp, npair, nchunk;

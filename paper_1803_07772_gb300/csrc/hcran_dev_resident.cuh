@@ -41,22 +41,26 @@ struct RView {
 struct RScratch {
   float *xch0, *xch1;  // per-CTA partial sums, by iteration parity
   float *xtot;         // their totals over the cluster
-  double *xi, *zeta;
+  float *xih, *xil;    // xi' as (hi, lo) float pairs
+  float *lzh, *lzl;    // log2 zeta' as (hi, lo) float pairs
   float *pmf, *xscale, *psi;  // pmax_m, 1 / (ln2 mask_m), Psi_k
 };
 
-__device__ __forceinline__ RScratch res_scratch(float *dyn, const KDims &kd) {
-  float *b = dyn + al4(kd.KSmax > 0 ? kd.KSmax : 1);
+__device__ __forceinline__ RScratch res_scratch(const KDims &kd) {
+  float *b = hcran_dyn + al4(kd.KSmax > 0 ? kd.KSmax : 1);
   const int xf = res_xch_floats(kd);
   RScratch s;
   s.xch0 = b;
   s.xch1 = b + xf;
   s.xtot = b + 2 * xf;
   b += 3 * xf;
-  s.xi = reinterpret_cast<double *>(b);
-  b += 2 * al4(kd.Mmax);
-  s.zeta = reinterpret_cast<double *>(b);
-  b += 2 * al4(kd.KSmax > 0 ? kd.KSmax : 1);
+  const int m4 = (int)al4(kd.Mmax), s4 = (int)al4(kd.KSmax > 0 ? kd.KSmax : 1);
+  s.xih = b;
+  s.xil = b + m4;
+  b += 2 * m4;
+  s.lzh = b;
+  s.lzl = b + s4;
+  b += 2 * s4;
   s.pmf = b;
   b += al4(kd.Mmax);
   s.xscale = b;
@@ -65,13 +69,31 @@ __device__ __forceinline__ RScratch res_scratch(float *dyn, const KDims &kd) {
   return s;
 }
 
-__device__ __forceinline__ RView res_view(float *b, const Ctx &c, int Nc) {
+// geometry of the resident region: offset in the dynamic shared memory and
+// the sizes the array offsets follow from
+struct RGeom {
+  int base, Nc, Rs, Mi, NW;
+};
+__device__ __forceinline__ RGeom res_geom(const Ctx &c, const KDims &kd) {
+  RGeom g;
+  g.base = (int)dyn_head_floats(kd);
+  g.Nc = c.n1 - c.n0;
+  g.Rs = res_row_stride(c.M, c.l);
+  g.Mi = c.M * c.npair;
+  g.NW = (g.Mi + 31) / 32;
+  return g;
+}
+
+// The views are rebuilt inside every (inlined) stage from the geometry, so a
+// stage keeps only the pointers it uses and they stay shared-memory pointers.
+__device__ __forceinline__ RView res_view(const Ctx &c, const RGeom &gm) {
   RView r;
-  const int M = c.M, Up = c.Up;
+  float *b = hcran_dyn + gm.base;
+  const int M = c.M, Up = c.Up, Nc = gm.Nc;
   r.Nc = Nc;
-  r.Rs = res_row_stride(M, c.l);
-  r.Mi = M * c.npair;
-  r.NW = (r.Mi + 31) / 32;
+  r.Rs = gm.Rs;
+  r.Mi = gm.Mi;
+  r.NW = gm.NW;
   r.slab = b; b += (size_t)Nc * M * r.Rs;
   const size_t su = (size_t)Nc * Up;
   r.k = reinterpret_cast<int *>(b); b += su;
@@ -112,7 +134,8 @@ __device__ __forceinline__ void ff_add(float &hi, float &lo, float s) {
 }
 
 // global -> shared at the start of a dual loop (subcarriers n0 .. n0+Nc-1)
-__device__ __forceinline__ void load_res(const Ctx &c, const RView &r, int n0) {
+__device__ __forceinline__ void load_res(const Ctx &c, const RGeom &gm, int n0) {
+  const RView r = res_view(c, gm);
   const int M = c.M, Up = c.Up, Rs = r.Rs, Nc = r.Nc;
   const int q = Up / 4, rows = Nc * M;
   const float4 *src = reinterpret_cast<const float4 *>(c.slab + (size_t)n0 * M * Up);
@@ -145,7 +168,8 @@ __device__ __forceinline__ void load_res(const Ctx &c, const RView &r, int n0) {
 }
 
 // shared -> global at the end: powers and the committed SIC multipliers
-__device__ __forceinline__ void store_res(const Ctx &c, const RView &r, int n0, int zc) {
+__device__ __forceinline__ void store_res(const Ctx &c, const RGeom &gm, int n0, int zc) {
+  const RView r = res_view(c, gm);
   const int Up = c.Up, Mi = r.Mi;
   const float *zh = zc ? r.zh1 : r.zh0, *zl = zc ? r.zl1 : r.zl0;
   for (int e = threadIdx.x; e < r.Nc * Up; e += kThreads)
@@ -188,7 +212,8 @@ __device__ __forceinline__ void clear_sub(const Ctx &c, const RView &r, int t, i
 }
 
 // entry: RRH totals at p^0
-__device__ __forceinline__ void stage_totals(const Ctx &c, const RView &r, const GIt &gi) {
+__device__ __forceinline__ void stage_totals(const Ctx &c, const RGeom &gm, const GIt &gi) {
+  const RView r = res_view(c, gm);
   const int M = c.M, l = c.l, Up = c.Up;
   int t = gi.t0, m = gi.m0;
   for (int h = threadIdx.x; h < r.Nc * M; h += kThreads, group_next(gi, M, t, m)) {
@@ -216,11 +241,76 @@ __device__ __forceinline__ float kkt_power(const PowerCtx &q, const float *szeta
   return fmaxf(pv, q.fl);
 }
 
+// KKT power of the L slots of one group, all values in registers (L <= 4 at
+// compile time); writes the new powers, returns the group total
+template <int L>
+__device__ __forceinline__ float power_group(const RView &r, const PowerCtx &q, const float *szeta, int base,
+                                             float &dmax) {
+  int k[L];
+  float pi[L], g[L], p[L], wa[L], pl[L];
+#pragma unroll
+  for (int s = 0; s < L; s++) {
+    const int e = base + s;
+    k[s] = r.k[e];
+    pi[s] = r.pi[e];
+    g[s] = r.g[e];
+    p[s] = r.p[e];
+    wa[s] = r.wa[e];
+    pl[s] = r.pl[e];
+  }
+  float own[L];  // weaker users of the same (m, n) that hear slot s
+  own[L - 1] = 0.f;
+#pragma unroll
+  for (int s = L - 2; s >= 0; s--) own[s] = own[s + 1] + pi[s + 1] * g[s + 1];
+  float tot = 0.f;
+#pragma unroll
+  for (int s = L - 1; s >= 0; s--) {
+    if (k[s] < 0) continue;
+    const float pv = kkt_power(q, szeta, k[s], own[s], wa[s], pl[s]);
+    dmax = fmaxf(dmax, fabsf(pv - p[s]) * q.im);
+    r.p[base + s] = pv;
+    tot += pv;
+  }
+  return tot;
+}
+
+template <int L>
+__device__ __forceinline__ float power_stage_l(const Ctx &c, const Shared &sh, const RView &r, const float *szeta,
+                                               const GIt &gi) {
+  const int M = c.M, Up = c.Up, G = r.Nc * M;
+  PowerCtx q;
+  q.Ke = c.Ke;
+  float dmax = 0.f;
+  int t = gi.t0, m = gi.m0;
+  for (int h = threadIdx.x; h < G; h += kThreads, group_next(gi, M, t, m)) {
+    const int base = t * Up + m * L;
+    q.PIO = r.pio[h];
+    q.SP = r.Sp[h];
+    q.SM = r.Sm[h];
+    q.qe = sh.qeta[m];
+    q.xf = sh.xif[m];
+    q.mk = sh.maskf[m];
+    q.fl = sh.floorf[m];
+    q.im = sh.invmask[m];
+    r.Pt[h] = power_group<L>(r, q, szeta, base, dmax);
+    clear_sub(c, r, t, m);
+  }
+  return dmax;
+}
+
 // power stage: KKT power of the l slots of (n, m) from the sums of the last
 // link / rows stages and the current multipliers; RRH total at the new point.
 // Returns the thread's max |p_new - p| / mask.
-__device__ __forceinline__ float stage_power(const Ctx &c, const Shared &sh, const RView &r, const float *szeta,
+__device__ __forceinline__ float stage_power(const Ctx &c, const Shared &sh, const RGeom &gm, const float *szeta,
                                              const GIt &gi) {
+  const RView r = res_view(c, gm);
+  switch (c.l) {
+    case 1: return power_stage_l<1>(c, sh, r, szeta, gi);
+    case 2: return power_stage_l<2>(c, sh, r, szeta, gi);
+    case 3: return power_stage_l<3>(c, sh, r, szeta, gi);
+    case 4: return power_stage_l<4>(c, sh, r, szeta, gi);
+    default: break;
+  }
   const int M = c.M, l = c.l, Up = c.Up, G = r.Nc * M;
   PowerCtx q;
   q.Ke = c.Ke;
@@ -236,47 +326,18 @@ __device__ __forceinline__ float stage_power(const Ctx &c, const Shared &sh, con
     q.mk = sh.maskf[m];
     q.fl = sh.floorf[m];
     q.im = sh.invmask[m];
-    float tot = 0.f;
-    if (l <= 4) {
-      int k[4];
-      float pi[4], g[4], p[4], wa[4], pl[4];
-#pragma unroll
-      for (int s = 0; s < 4; s++)
-        if (s < l) {
-          const int e = base + s;
-          k[s] = r.k[e];
-          pi[s] = r.pi[e];
-          g[s] = r.g[e];
-          p[s] = r.p[e];
-          wa[s] = r.wa[e];
-          pl[s] = r.pl[e];
-        }
-      float own = 0.f;  // weaker users of the same (m, n) that hear slot s
-#pragma unroll
-      for (int s = 3; s >= 0; s--)
-        if (s < l) {
-          if (k[s] >= 0) {
-            const float pv = kkt_power(q, szeta, k[s], own, wa[s], pl[s]);
-            dmax = fmaxf(dmax, fabsf(pv - p[s]) * q.im);
-            r.p[base + s] = pv;
-            tot += pv;
-          }
-          own += pi[s] * g[s];
-        }
-    } else {
-      float own = 0.f;
-      for (int s = l - 1; s >= 0; s--) {
-        const int e = base + s;
-        const int k = r.k[e];
-        const float pis = r.pi[e], gs = r.g[e];
-        if (k >= 0) {
-          const float pv = kkt_power(q, szeta, k, own, r.wa[e], r.pl[e]);
-          dmax = fmaxf(dmax, fabsf(pv - r.p[e]) * q.im);
-          r.p[e] = pv;
-          tot += pv;
-        }
-        own += pis * gs;
+    float tot = 0.f, own = 0.f;
+    for (int s = l - 1; s >= 0; s--) {
+      const int e = base + s;
+      const int k = r.k[e];
+      const float pis = r.pi[e], gs = r.g[e];
+      if (k >= 0) {
+        const float pv = kkt_power(q, szeta, k, own, r.wa[e], r.pl[e]);
+        dmax = fmaxf(dmax, fabsf(pv - r.p[e]) * q.im);
+        r.p[e] = pv;
+        tot += pv;
       }
+      own += pis * gs;
     }
     r.Pt[h] = tot;
     clear_sub(c, r, t, m);
@@ -313,10 +374,117 @@ __device__ __forceinline__ bool sic_step(float sigma, float scale, float delta, 
   return hi != 0.f;
 }
 
+// set bits i0 + pr of subcarrier t's nonzero-multiplier mask (at most 28 bits,
+// possibly straddling two words)
+__device__ __forceinline__ void mark_nonzero(const RView &r, int t, int i0, unsigned bits) {
+  if (!bits) return;
+  const unsigned long long wide = (unsigned long long)bits << (i0 & 31);
+  unsigned *wd = r.nz + t * r.NW + (i0 >> 5);
+  if ((unsigned)wide) atomicOr(wd, (unsigned)wide);
+  if ((unsigned)(wide >> 32)) atomicOr(wd + 1, (unsigned)(wide >> 32));
+}
+
+// link of one group with L <= 4 slots, every slot value in registers
+template <int L>
+__device__ __forceinline__ void link_group(const RView &r, const float *szeta, int t, int m, int M, int Rs,
+                                           int base, int Ks, int Ke, float sigma, float scale, float delta,
+                                           const float *zh, const float *zl, float *nh, float *nl) {
+  constexpr int NP = L * (L - 1) / 2;
+  int k[L];
+  float p[L], g[L], gi[L], wa[L];
+#pragma unroll
+  for (int s = 0; s < L; s++) {
+    const int e = base + s;
+    k[s] = r.k[e];
+    p[s] = r.p[e];
+    g[s] = r.g[e];
+    gi[s] = r.gi[e];
+    wa[s] = r.wa[e];
+  }
+  float zhv[NP > 0 ? NP : 1], zlv[NP > 0 ? NP : 1];
+#pragma unroll
+  for (int pr = 0; pr < NP; pr++) {
+    zhv[pr] = zh[pr];
+    zlv[pr] = zl[pr];
+  }
+  // interference of the L slots in one pass over the slab rows (own entry is
+  // zero), two partial sums per slot
+  const float *Pt = r.Pt + t * M;
+  const float *SL = r.slab + (size_t)t * M * Rs + m * L;
+  float xa[L], xb[L];
+#pragma unroll
+  for (int s = 0; s < L; s++) xa[s] = xb[s] = 0.f;
+  int j = 0;
+  for (; j + 1 < M; j += 2) {
+    const float pa = Pt[j], pb = Pt[j + 1];
+    const float *ra = SL + j * Rs, *rb = ra + Rs;
+#pragma unroll
+    for (int s = 0; s < L; s++) {
+      xa[s] += ra[s] * pa;
+      xb[s] += rb[s] * pb;
+    }
+  }
+  if (j < M) {
+    const float pa = Pt[j];
+    const float *ra = SL + j * Rs;
+#pragma unroll
+    for (int s = 0; s < L; s++) xa[s] += ra[s] * pa;
+  }
+  float X[L];
+#pragma unroll
+  for (int s = 0; s < L; s++) X[s] = xa[s] + xb[s];
+  float intra = 0.f;
+#pragma unroll
+  for (int s = 0; s < L; s++) {
+    const int e = base + s;
+    const float pi = k[s] >= 0 ? slot_price(r, szeta, t, Ks, Ke, sigma, e, k[s], p[s], g[s], wa[s], intra, X[s])
+                               : 0.f;
+    r.pi[e] = pi;
+    intra += p[s];  // empty slots hold p = 0
+  }
+  unsigned bits = 0u;
+  int pr = 0;
+#pragma unroll
+  for (int a = 0; a < L; a++)
+#pragma unroll
+    for (int b = a + 1; b < L; b++, pr++) {
+      float hi = zhv[pr], lo = zlv[pr];
+      if (k[a] >= 0 && k[b] >= 0 && sic_step(sigma, scale, delta, X[a], gi[a], X[b], gi[b], hi, lo))
+        bits |= 1u << pr;
+      nh[pr] = hi;
+      nl[pr] = lo;
+    }
+  mark_nonzero(r, t, m * NP, bits);
+}
+
+template <int L>
+__device__ __forceinline__ void link_stage_l(const Ctx &c, const Shared &sh, const RView &r, const float *szeta,
+                                             float delta, int zc, const GIt &gi) {
+  const int M = c.M, Up = c.Up, Rs = r.Rs, Ks = c.Ks, Ke = c.Ke, G = r.Nc * M;
+  constexpr int NP = L * (L - 1) / 2;
+  const float sigma = c.sigma;
+  const float *zh0 = zc ? r.zh1 : r.zh0, *zl0 = zc ? r.zl1 : r.zl0;
+  float *nh0 = zc ? r.zh0 : r.zh1, *nl0 = zc ? r.zl0 : r.zl1;
+  int t = gi.t0, m = gi.m0;
+  for (int h = threadIdx.x; h < G; h += kThreads, group_next(gi, M, t, m)) {
+    const int o = t * r.Mi + m * NP;
+    link_group<L>(r, szeta, t, m, M, Rs, t * Up + m * L, Ks, Ke, sigma, sh.sicscale[m], delta, zh0 + o, zl0 + o,
+                  nh0 + o, nl0 + o);
+  }
+}
+
 // link stage at the point in r.p (Sec. II-A SINR with the SIC order), then the
 // SIC step of (n, m): generation zc -> zc ^ 1 with step delta
-__device__ __forceinline__ void stage_link(const Ctx &c, const Shared &sh, const RView &r, const float *szeta,
+__device__ __forceinline__ void stage_link(const Ctx &c, const Shared &sh, const RGeom &gm, const float *szeta,
                                            float delta, int zc, const GIt &gi) {
+  const RView r = res_view(c, gm);
+  switch (c.l) {
+    case 1: link_stage_l<1>(c, sh, r, szeta, delta, zc, gi); return;
+    case 2: link_stage_l<2>(c, sh, r, szeta, delta, zc, gi); return;
+    case 3: link_stage_l<3>(c, sh, r, szeta, delta, zc, gi); return;
+    case 4: link_stage_l<4>(c, sh, r, szeta, delta, zc, gi); return;
+    default: break;
+  }
   const int M = c.M, l = c.l, Up = c.Up, Rs = r.Rs, np = c.npair, Ks = c.Ks, Ke = c.Ke, G = r.Nc * M;
   const float sigma = c.sigma;
   const float *zh0 = zc ? r.zh1 : r.zh0, *zl0 = zc ? r.zl1 : r.zl0;
@@ -330,83 +498,38 @@ __device__ __forceinline__ void stage_link(const Ctx &c, const Shared &sh, const
     const float *zh = zh0 + o, *zl = zl0 + o;
     float *nh = nh0 + o, *nl = nl0 + o;
     const float scale = sh.sicscale[m];
+    float intra = 0.f;
+    for (int s = 0; s < l; s++) {
+      const int e = base + s;
+      const int k = r.k[e];
+      const float ps = r.p[e];
+      float X = 0.f, pi = 0.f;
+      for (int j = 0; j < M; j++) X += SL[j * Rs + s] * Pt[j];
+      if (k >= 0) pi = slot_price(r, szeta, t, Ks, Ke, sigma, e, k, ps, r.g[e], r.wa[e], intra, X);
+      r.pi[e] = pi;
+      r.X[e] = X;
+      intra += ps;
+    }
     unsigned bits = 0u;
-    if (l <= 4) {
-      // interference of the l slots in one pass over the slab rows (own entry is zero)
-      float X[4] = {0.f, 0.f, 0.f, 0.f};
-      for (int j = 0; j < M; j++) {
-        const float pt = Pt[j];
-        const float *row = SL + j * Rs;
-#pragma unroll
-        for (int s = 0; s < 4; s++)
-          if (s < l) X[s] += row[s] * pt;
+    int pr = 0;
+    for (int a = 0; a < l; a++)
+      for (int b = a + 1; b < l; b++, pr++) {
+        const int ea = base + a, eb = base + b;
+        float hi = zh[pr], lo = zl[pr];
+        if (r.k[ea] >= 0 && r.k[eb] >= 0 &&
+            sic_step(sigma, scale, delta, r.X[ea], r.gi[ea], r.X[eb], r.gi[eb], hi, lo))
+          bits |= 1u << pr;
+        nh[pr] = hi;
+        nl[pr] = lo;
       }
-      int k[4];
-      float gi4[4];
-      float intra = 0.f;
-#pragma unroll
-      for (int s = 0; s < 4; s++)
-        if (s < l) {
-          const int e = base + s;
-          k[s] = r.k[e];
-          gi4[s] = r.gi[e];
-          const float ps = r.p[e];
-          float pi = 0.f;
-          if (k[s] >= 0) pi = slot_price(r, szeta, t, Ks, Ke, sigma, e, k[s], ps, r.g[e], r.wa[e], intra, X[s]);
-          r.pi[e] = pi;
-          intra += ps;  // empty slots hold p = 0
-        }
-      int pr = 0;
-#pragma unroll
-      for (int a = 0; a < 4; a++)
-#pragma unroll
-        for (int b = a + 1; b < 4; b++)
-          if (b < l) {
-            float hi = zh[pr], lo = zl[pr];
-            if (k[a] >= 0 && k[b] >= 0 && sic_step(sigma, scale, delta, X[a], gi4[a], X[b], gi4[b], hi, lo))
-              bits |= 1u << pr;
-            nh[pr] = hi;
-            nl[pr] = lo;
-            pr++;
-          }
-    } else {
-      float intra = 0.f;
-      for (int s = 0; s < l; s++) {
-        const int e = base + s;
-        const int k = r.k[e];
-        const float ps = r.p[e];
-        float X = 0.f, pi = 0.f;
-        for (int j = 0; j < M; j++) X += SL[j * Rs + s] * Pt[j];
-        if (k >= 0) pi = slot_price(r, szeta, t, Ks, Ke, sigma, e, k, ps, r.g[e], r.wa[e], intra, X);
-        r.pi[e] = pi;
-        r.X[e] = X;
-        intra += ps;
-      }
-      int pr = 0;
-      for (int a = 0; a < l; a++)
-        for (int b = a + 1; b < l; b++, pr++) {
-          const int ea = base + a, eb = base + b;
-          float hi = zh[pr], lo = zl[pr];
-          if (r.k[ea] >= 0 && r.k[eb] >= 0 &&
-              sic_step(sigma, scale, delta, r.X[ea], r.gi[ea], r.X[eb], r.gi[eb], hi, lo))
-            bits |= 1u << pr;
-          nh[pr] = hi;
-          nl[pr] = lo;
-        }
-    }
-    if (bits) {  // bits i0 + pr of subcarrier n's mask (np <= 28 bits, may straddle two words)
-      const int i0 = m * np;
-      const unsigned long long wide = (unsigned long long)bits << (i0 & 31);
-      unsigned *wd = r.nz + t * r.NW + (i0 >> 5);
-      if ((unsigned)wide) atomicOr(wd, (unsigned)wide);
-      if ((unsigned)(wide >> 32)) atomicOr(wd + 1, (unsigned)(wide >> 32));
-    }
+    mark_nonzero(r, t, m * np, bits);
   }
 }
 
 // rows stage per (n, j): pio = row j of the slab . pi, and the SIC+ / SIC-
 // sums of row j over the nonzero multipliers of n (generation zn)
-__device__ __forceinline__ void stage_rows(const Ctx &c, const Shared &sh, const RView &r, int zn, const GIt &gi) {
+__device__ __forceinline__ void stage_rows(const Ctx &c, const Shared &sh, const RGeom &gm, int zn, const GIt &gi) {
+  const RView r = res_view(c, gm);
   const int M = c.M, Up = c.Up, Rs = r.Rs, q4 = Up / 4;
   int t = gi.t0, j = gi.m0;
   for (int h = threadIdx.x; h < r.Nc * M; h += kThreads, group_next(gi, M, t, j)) {
@@ -426,14 +549,22 @@ __device__ __forceinline__ void stage_rows(const Ctx &c, const Shared &sh, const
     const float *ginv = r.gi + t * Up;
     for (int w = 0; w < r.NW; w++) {
       unsigned bits = r.nz[t * r.NW + w];
-      while (bits) {
-        const int i = w * 32 + __ffs(bits) - 1;
+      while (bits) {  // two nonzero multipliers per pass, in bit order
+        const int i1 = w * 32 + __ffs(bits) - 1;
         bits &= bits - 1u;
-        const int ua = sh.item_a[i], ub = sh.item_b[i];
-        const float z = zh[i];
-        const float tt = row[ua] * (z * ginv[ua]) - row[ub] * (z * ginv[ub]);
-        if (tt > 0.f) sp += tt;
-        else sm -= tt;
+        const bool two = bits != 0u;
+        const int i2 = two ? w * 32 + __ffs(bits) - 1 : i1;
+        if (two) bits &= bits - 1u;
+        const int ua1 = sh.item_a[i1], ub1 = sh.item_b[i1], ua2 = sh.item_a[i2], ub2 = sh.item_b[i2];
+        const float z1 = zh[i1], z2 = zh[i2];
+        const float t1 = row[ua1] * (z1 * ginv[ua1]) - row[ub1] * (z1 * ginv[ub1]);
+        const float t2 = row[ua2] * (z2 * ginv[ua2]) - row[ub2] * (z2 * ginv[ub2]);
+        if (t1 > 0.f) sp += t1;
+        else sm -= t1;
+        if (two) {
+          if (t2 > 0.f) sp += t2;
+          else sm -= t2;
+        }
       }
     }
     r.pio[h] = (a0 + a1) + (a2 + a3);
@@ -443,27 +574,42 @@ __device__ __forceinline__ void stage_rows(const Ctx &c, const Shared &sh, const
 }
 
 // this CTA's residual sums over its subcarriers into xv: RRH totals [M],
-// streaming rates [Ks], streaming alphas [Ks]; then the max |dp| / mask
-__device__ __forceinline__ void res_partials(const Ctx &c, Shared &sh, const RView &r, float *xv, float dl) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int M = c.M, Ks = c.Ks;
-  for (int q = warp; q < M + 2 * Ks; q += kWarps) {
-    const float *src;
-    int stride;
-    if (q < M) {
-      src = r.Pt + q;
-      stride = M;
-    } else if (q < M + Ks) {
-      src = r.sr + (q - M);
-      stride = Ks;
-    } else {
-      src = r.sa + (q - M - Ks);
-      stride = Ks;
-    }
+// streaming rates [Ks], streaming alphas [Ks].  Teams of 8 lanes, one sum per
+// team, lanes over the subcarriers and a 3-step shuffle tree (fixed order).
+// The warp's max |dp| / mask goes to sh.redf.
+__device__ __forceinline__ void res_partials(const Ctx &c, Shared &sh, const RGeom &gm, float *xv, float dl) {
+  const RView r = res_view(c, gm);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, sub = lane & 7;
+  const int M = c.M, Ks = c.Ks, nq = M + 2 * Ks, Nc = r.Nc;
+  for (int q0 = warp * 4; q0 < nq; q0 += kThreads / 8) {  // warp-uniform trip count
+    const int q = q0 + (lane >> 3);
     float a = 0.f;
-    for (int t = lane; t < r.Nc; t += 32) a += src[t * stride];
-    a = warp_sum(a);
-    if (lane == 0) xv[q] = a;
+    if (q < nq) {
+      const float *src;
+      int stride;
+      if (q < M) {
+        src = r.Pt + q;
+        stride = M;
+      } else if (q < M + Ks) {
+        src = r.sr + (q - M);
+        stride = Ks;
+      } else {
+        src = r.sa + (q - M - Ks);
+        stride = Ks;
+      }
+      float a0 = 0.f, a1 = 0.f;
+      int t = sub;
+      for (; t + 8 < Nc; t += 16) {
+        a0 += src[t * stride];
+        a1 += src[(t + 8) * stride];
+      }
+      if (t < Nc) a0 += src[t * stride];
+      a = a0 + a1;
+    }
+    a += __shfl_xor_sync(0xffffffffu, a, 4);
+    a += __shfl_xor_sync(0xffffffffu, a, 2);
+    a += __shfl_xor_sync(0xffffffffu, a, 1);
+    if (sub == 0 && q < nq) xv[q] = a;
   }
   dl = warp_max(dl);
   if (lane == 0) sh.redf[warp] = dl;
@@ -478,18 +624,23 @@ __device__ int dual_loop_res(const Ctx &c, Shared &sh, float *dyn, const KDims &
                              const Tol &tol, long long *cyc, unsigned &phase, unsigned &pending) {
   const int Vmax = tol.max_dual > 0 ? tol.max_dual : 1;
   const int M = c.M, Ks = c.Ks;
-  const RView r = res_view(dyn + dyn_head_floats(kd), c, c.n1 - c.n0);
-  const RScratch x = res_scratch(dyn, kd);
+  const RGeom r = res_geom(c, kd);
+  const RScratch x = res_scratch(kd);
   const long long t0 = clock64();
   const GIt gi = group_iter(M);
   load_res(c, r, c.n0);
   for (int m = threadIdx.x; m < M; m += kThreads) {
-    x.xi[m] = c.xi[m];
+    const float hi = (float)c.xi[m];
+    x.xih[m] = hi;
+    x.xil[m] = (float)(c.xi[m] - (double)hi);
     x.pmf[m] = (float)c.pmax[m];
     x.xscale[m] = 1.f / (LN2F * sh.maskf[m]);
   }
   for (int k = threadIdx.x; k < Ks; k += kThreads) {
-    x.zeta[k] = c.zeta[k];
+    const double lz = log2(c.zeta[k]);
+    const float hi = (float)lz;
+    x.lzh[k] = hi;
+    x.lzl[k] = (float)(lz - (double)hi);
     x.psi[k] = sh_psi(c, k);
   }
   __syncthreads();
@@ -509,10 +660,9 @@ __device__ int dual_loop_res(const Ctx &c, Shared &sh, float *dyn, const KDims &
     const int nx = M + 2 * Ks;
     res_partials(c, sh, r, xv, dl);
     __syncthreads();
-    if (threadIdx.x == 0) {
-      float d = sh.redf[0];
-      for (int i = 1; i < kWarps; i++) d = fmaxf(d, sh.redf[i]);
-      xv[nx] = d;
+    if (threadIdx.x < 32) {
+      const float d = warp_max(threadIdx.x < kWarps ? sh.redf[threadIdx.x] : 0.f);
+      if (threadIdx.x == 0) xv[nx] = d;
     }
     const float *xt = xv;
     if (c.csize > 1) {
@@ -520,8 +670,13 @@ __device__ int dual_loop_res(const Ctx &c, Shared &sh, float *dyn, const KDims &
       // rewritten two iterations later, after that barrier
       inst_sync(c);
       for (int i = threadIdx.x; i <= nx; i += kThreads) {
-        float t = peer(xv, 0)[i];
-        for (int q = 1; q < c.csize; q++) t = i < nx ? t + peer(xv, q)[i] : fmaxf(t, peer(xv, q)[i]);
+        float v[8];
+#pragma unroll
+        for (int q = 0; q < 8; q++) v[q] = q < c.csize ? peer(xv, q)[i] : 0.f;
+        float t = v[0];
+#pragma unroll
+        for (int q = 1; q < 8; q++)
+          if (q < c.csize) t = i < nx ? t + v[q] : fmaxf(t, v[q]);
         x.xtot[i] = t;
       }
       xt = x.xtot;
@@ -529,27 +684,41 @@ __device__ int dual_loop_res(const Ctx &c, Shared &sh, float *dyn, const KDims &
     __syncthreads();
     const float d = xt[nx];
     if ((v > 0 && d < (float)tol.tol_dual) || v >= Vmax) break;
+    // projected subgradient steps in FP32, accumulated in (hi, lo) float
+    // pairs: xi' on threads 0 .. M-1 (M <= kMaxM), zeta' (in log2 scale, where
+    // the multiplicative step of C13-hat is a sum) on threads kMaxM and up
     const float delta = rsqrtf((float)v + 1.f);
-    for (int t = threadIdx.x; t < M + Ks; t += kThreads) {
-      if (t < M) {
-        const int m = t;
-        const float pm = x.pmf[m];
-        const float step = delta * ((xt[m] - pm) / pm) * x.xscale[m];
-        double xm = x.xi[m];
-        if (xm != 0.0 || step > 0.f) {
-          xm += (double)step;
-          xm = xm > 0.0 ? xm : 0.0;
-          x.xi[m] = xm;
+    if (threadIdx.x < M) {
+      const int m = threadIdx.x;
+      const float pm = x.pmf[m];
+      const float step = delta * ((xt[m] - pm) / pm) * x.xscale[m];
+      float hi = x.xih[m], lo = x.xil[m];
+      if (hi != 0.f || step > 0.f) {
+        ff_add(hi, lo, step);
+        if (!(hi > 0.f)) {
+          hi = 0.f;
+          lo = 0.f;
         }
-        sh.xif[m] = (float)xm;
-      } else {
-        const int ks = t - M;
-        const float rr = xt[M + ks], as = xt[M + Ks + ks];
-        const float e = fminf(fmaxf((x.psi[ks] - rr) / fmaxf(as, (float)kZetaAsumMin), -1.f), 1.f);
-        const double z = fmin(fmax(x.zeta[ks] * (double)exp2f(e), kZetaMin), kZetaMax);
-        x.zeta[ks] = z;
-        szeta[ks] = (float)z;
+        x.xih[m] = hi;
+        x.xil[m] = lo;
       }
+      sh.xif[m] = hi;
+    }
+    for (int ks = (int)threadIdx.x - kMaxM; ks >= 0 && ks < Ks; ks += kThreads - kMaxM) {
+      const float rr = xt[M + ks], as = xt[M + Ks + ks];
+      const float e = fminf(fmaxf((x.psi[ks] - rr) / fmaxf(as, (float)kZetaAsumMin), -1.f), 1.f);
+      float hi = x.lzh[ks], lo = x.lzl[ks];
+      ff_add(hi, lo, e);
+      if (hi < kLog2ZetaMin) {
+        hi = kLog2ZetaMin;
+        lo = 0.f;
+      } else if (hi > kLog2ZetaMax) {
+        hi = kLog2ZetaMax;
+        lo = 0.f;
+      }
+      x.lzh[ks] = hi;
+      x.lzl[ks] = lo;
+      szeta[ks] = exp2f(hi) * (1.f + lo * LN2F);
     }
     __syncthreads();
     const long long t2 = clock64();
@@ -568,8 +737,8 @@ __device__ int dual_loop_res(const Ctx &c, Shared &sh, float *dyn, const KDims &
   }
   store_res(c, r, c.n0, zc);
   if (c.crank == 0) {
-    for (int m = threadIdx.x; m < M; m += kThreads) c.xi[m] = x.xi[m];
-    for (int k = threadIdx.x; k < Ks; k += kThreads) c.zeta[k] = x.zeta[k];
+    for (int m = threadIdx.x; m < M; m += kThreads) c.xi[m] = (double)x.xih[m] + (double)x.xil[m];
+    for (int k = threadIdx.x; k < Ks; k += kThreads) c.zeta[k] = exp2((double)x.lzh[k] + (double)x.lzl[k]);
   }
   // gamma, pi, X, totals and SIC sums at the final point for the later phases
   link_all<kLinkOnly>(c, sh, dyn, kd, szeta, 0.f, phase, pending);

@@ -219,7 +219,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                  InstOut *outs, Tol tol, KDims kd, int *counter) {
   __shared__ Shared sh;
   __shared__ Ctx sc;
-  extern __shared__ __align__(16) float dyn[];
+  float *dyn = hcran_dyn;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // a launch with clusters solves each instance on one cluster; CTA r of the
   // cluster owns a contiguous share of the subcarriers
