@@ -196,8 +196,14 @@ def run_gpu(args):
         g = torch.from_numpy(gains).to(dev)
     torch.cuda.synchronize(dev)
 
+    # schedule: the planner's smallest-cluster choice, then the autotuner
+    # (untimed); the timed steps replay one CUDA graph of the class launches
+    planned = solver.schedule()
+    if not args.no_autotune:
+        solver.autotune(g, tol, max_dual_probe=60)
+    sched = solver.schedule()
     for _ in range(args.warmup):
-        solver.solve(g, tol)
+        solver.solve_graph(g, tol)
     stream.synchronize()
 
     if world > 1:
@@ -210,7 +216,7 @@ def run_gpu(args):
     ev0.record(stream)
     launches = 0
     for _ in range(args.steps):
-        solver.solve(g, tol)
+        solver.solve_graph(g, tol)
         launches += solver.launches()
     ev1.record(stream)
     stream.synchronize()
@@ -266,7 +272,11 @@ def run_gpu(args):
                        "sizes": "M~U{3..16}, N~U{16..256}, K~U{10..120}, 30% streaming, l=3",
                        "precision": "FP32 SINR/power/prices, FP64 Dinkelbach q, F(q), multipliers",
                        "l2": "inputs larger than L2 (%.2f GB of gains per step)" % (gains.nbytes / 1e9),
-                       "parallelism": "replicas" if world == 1 else "dp%d" % world},
+                       "parallelism": "replicas" if world == 1 else "dp%d" % world,
+                       "schedule": {("streamed" if k == 0 else "cluster%d" % k): int(v)
+                                    for k, v in zip(*np.unique(sched, return_counts=True))},
+                       "schedule_changed_by_autotuner": int(np.sum(sched != planned)),
+                       "launch": "CUDA graph, one persistent launch per cluster size"},
             "gpu_launches": launches,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
@@ -320,6 +330,7 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--instances", type=int, default=4096)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the planner's schedule")
     ap.add_argument("--profile-case", action="store_true",
                     help="one solve of the first 152 instances with short caps (1 Dinkelbach "
                          "iteration, 2 SCALE passes, 100 dual iterations): the small case for ncu")

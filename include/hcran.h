@@ -163,6 +163,36 @@ int hcran_last_launch_count(hcran_t h, int32_t *launches);
  * argument. */
 int hcran_get_schedule(hcran_t h, int32_t *cluster_size);
 
+/* Replace the schedule: cluster_size[b] in {1, 2, 4, 8} (a cluster of that
+ * many CTAs with the dual-loop state resident in their shared memory; at
+ * least one subcarrier per CTA, and the state must fit) or 0 (one CTA
+ * streaming from global memory).  An instance whose class would exceed
+ * shared memory moves on to a larger cluster (hcran_get_schedule reports the
+ * result).  The next solve uploads the new plan to its workspace.  Returns
+ * HCRAN_EINVAL (schedule unchanged) on a NULL argument or an infeasible
+ * size. */
+int hcran_set_schedule(hcran_t h, const int32_t *cluster_size);
+
+/* Autotuner of the schedule.  For each cluster size in use (1, 2, 4) it times
+ * that class's launch against clusters twice as large on the class's first
+ * S instances in launch order (S = the class size, at most two waves of the
+ * current schedule), with one Dinkelbach iteration, one SCALE pass and
+ * exactly max_dual_probe dual iterations, and keeps the faster schedule.
+ * Probes overwrite the solution state in the workspace (a later solve starts
+ * afresh).  Synchronises the stream.  gains_dev and workspace as for
+ * hcran_solve; tol supplies tie_eps and q_init.  Returns HCRAN_EINVAL on bad
+ * arguments, HCRAN_ECUDA on a CUDA error. */
+int hcran_autotune(hcran_t h, const float *gains_dev, const hcran_tol *tol, void *workspace_dev, void *stream,
+                   int32_t max_dual_probe);
+
+/* hcran_solve through a CUDA graph: the launch sequence (one persistent
+ * launch per cluster size) is captured on the first call for a given
+ * (gains_dev, workspace, tol) and replayed by later calls with the same
+ * arguments; any change, or a new schedule, re-captures.  stream must be a
+ * created stream (not the legacy default stream, which cannot be captured).
+ * Same results as hcran_solve. */
+int hcran_solve_graph(hcran_t h, const float *gains_dev, const hcran_tol *tol, void *workspace_dev, void *stream);
+
 void hcran_destroy(hcran_t h);
 
 /* ---- allocation-free single-instance solve ----------------------------

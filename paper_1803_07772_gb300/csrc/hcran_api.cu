@@ -42,7 +42,83 @@ struct hcran_s {
   cudaStream_t last_stream = nullptr;
   int32_t last_launches = 0;
   std::vector<InstOut> outs_host;
+  bool plan_dirty = false;  // descriptors / order changed since they were uploaded
+  // captured launch sequence of hcran_solve_graph and the arguments it was captured for
+  cudaGraphExec_t graph = nullptr;
+  const void *graph_gains = nullptr, *graph_ws = nullptr;
+  hcran_tol graph_tol{};
+  ~hcran_s() {
+    if (graph) cudaGraphExecDestroy(graph);
+  }
 };
+
+// Launch classes from the per-instance classes h->cls: launch dimensions per
+// class (an instance that would push its class over the shared-memory limit
+// moves on to the next larger cluster), chunk counts, and the launch order
+// (classes largest cluster first; longest-processing-time order, largest
+// M*N*K*l first, inside a class).  Returns nonzero when the streamed class
+// does not fit shared memory either.
+static int build_classes(hcran_s *h) {
+  const int32_t n = h->n;
+  for (;;) {
+    bool moved = false;
+    for (int k = 0; k < kNumClasses; k++) h->classes[k] = LaunchClass();
+    for (int32_t b = 0; b < n; b++) {
+      const InstDesc &d = h->descs[b];
+      LaunchClass &L = h->classes[h->cls[b]];
+      const KDims one = h->cls[b] < kNumClasses - 1
+                            ? resident_kdims(d.M, d.l, d.Ks, d.N, class_csize(h->cls[b]))
+                            : KDims{slot_stride(d.M, d.l), d.M, d.npair, pair_stride(d.M, d.l), d.Ks, 0, 0, 0};
+      if (L.count == 0) L.kd = one;
+      else kdims_merge(L.kd, one);
+      L.count++;
+    }
+    for (int k = 0; k < kNumClasses - 1 && !moved; k++) {
+      LaunchClass &L = h->classes[k];
+      if (L.count == 0 || dyn_smem_bytes(L.kd) <= kMaxDynSmem) continue;
+      int worst = -1;  // the instance with the largest resident state of the class
+      int64_t wr = -1;
+      for (int32_t b = 0; b < n; b++)
+        if (h->cls[b] == k) {
+          const InstDesc &d = h->descs[b];
+          const int64_t r = res_floats(d.M, d.l, d.Ks, (d.N + class_csize(k) - 1) / class_csize(k));
+          if (r > wr) {
+            wr = r;
+            worst = b;
+          }
+        }
+      h->cls[worst] = k == 0 ? kNumClasses - 1 : k - 1;
+      moved = true;
+    }
+    if (!moved) break;
+  }
+  {  // streamed class: staging when the double buffers fit, else global reads
+    LaunchClass &L = h->classes[kNumClasses - 1];
+    if (L.count > 0 && plan_kdims(L.kd, int64_t(1) << 40) != 0) return 1;
+  }
+  for (int32_t b = 0; b < n; b++) {
+    InstDesc &d = h->descs[b];
+    d.nchunk = class_nchunk(d.N, d.K, class_csize(h->cls[b]));
+  }
+  h->order.resize(n);
+  std::iota(h->order.begin(), h->order.end(), 0);
+  std::stable_sort(h->order.begin(), h->order.end(), [&](int a, int b) {
+    if (h->cls[a] != h->cls[b]) return h->cls[a] < h->cls[b];
+    const InstDesc &x = h->descs[a], &y = h->descs[b];
+    return int64_t(x.N) * x.M * x.K * x.l > int64_t(y.N) * y.M * y.K * y.l;
+  });
+  for (int k = 0, first = 0; k < kNumClasses; k++) {
+    h->classes[k].csize = class_csize(k);
+    h->classes[k].first = first;
+    first += h->classes[k].count;
+  }
+  if (h->graph) {  // the captured launch sequence no longer matches
+    cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+  }
+  h->plan_dirty = true;
+  return 0;
+}
 
 static uint64_t al256(uint64_t x) { return (x + 255) & ~uint64_t(255); }
 
@@ -103,7 +179,6 @@ extern "C" int hcran_create(hcran_t *out, const hcran_config *cfgs, int32_t n,
       d.L = c.N * d.U;
       d.npair = c.l * (c.l - 1) / 2;
       h->cls[b] = pick_class(c.M, c.l, c.Ks, c.N);
-      d.nchunk = class_nchunk(c.N, c.K, class_csize(h->cls[b]));
       const int64_t cost = int64_t(c.N) * c.M * c.K;
       if (gain_offsets) {
         if (gain_offsets[b] < 0 || (gain_offsets[b] & 3)) { delete h; return HCRAN_EINVAL; }
@@ -118,50 +193,14 @@ extern "C" int hcran_create(hcran_t *out, const hcran_config *cfgs, int32_t n,
       for (int m = 0; m < c.M; m++) pc += c.Pc[m] + c.Pf[m];
       d.Pconst = pc;
     }
-    // launch dimensions per class; an instance that would push its class over
-    // the shared-memory limit moves on to the next larger cluster
-    for (;;) {
-      bool moved = false;
-      for (int k = 0; k < kNumClasses; k++) h->classes[k] = LaunchClass();
-      for (int32_t b = 0; b < n; b++) {
-        const hcran_config &c = cfgs[b];
-        LaunchClass &L = h->classes[h->cls[b]];
-        const KDims one = h->cls[b] < kNumClasses - 1
-                              ? resident_kdims(c.M, c.l, c.Ks, c.N, class_csize(h->cls[b]))
-                              : KDims{slot_stride(c.M, c.l), c.M, c.l * (c.l - 1) / 2, pair_stride(c.M, c.l),
-                                      c.Ks, 0, 0, 0};
-        if (L.count == 0) L.kd = one;
-        else kdims_merge(L.kd, one);
-        L.count++;
-      }
-      for (int k = 0; k < kNumClasses - 1 && !moved; k++) {
-        LaunchClass &L = h->classes[k];
-        if (L.count == 0 || dyn_smem_bytes(L.kd) <= kMaxDynSmem) continue;
-        int worst = -1;  // the instance with the largest resident state of the class
-        int64_t wr = -1;
-        for (int32_t b = 0; b < n; b++)
-          if (h->cls[b] == k) {
-            const int64_t r = res_floats(cfgs[b].M, cfgs[b].l, cfgs[b].Ks,
-                                         (cfgs[b].N + class_csize(k) - 1) / class_csize(k));
-            if (r > wr) { wr = r; worst = b; }
-          }
-        h->cls[worst] = k == 0 ? kNumClasses - 1 : k - 1;
-        h->descs[worst].nchunk = class_nchunk(cfgs[worst].N, cfgs[worst].K, class_csize(h->cls[worst]));
-        moved = true;
-      }
-      if (!moved) break;
-    }
-    {  // streamed class: staging when the double buffers fit, else global reads
-      LaunchClass &L = h->classes[kNumClasses - 1];
-      if (L.count > 0 && plan_kdims(L.kd, int64_t(1) << 40) != 0) { delete h; return HCRAN_EINVAL; }
-    }
-    // arenas (the chunk count of an instance depends on its class)
+    if (build_classes(h) != 0) { delete h; return HCRAN_EINVAL; }
+    // arenas (sized for any schedule of the instance)
     doff = foff = ioff = 0;
     for (int32_t b = 0; b < n; b++) {
       const hcran_config &c = cfgs[b];
       InstDesc &d = h->descs[b];
       const DLayout dl = dlayout(c.M, c.N, c.K, c.Ks, c.l);
-      const FLayout fl = flayout(c.M, c.N, c.K, c.l, d.nchunk);
+      const FLayout fl = flayout(c.M, c.N, c.K, c.l, nchunk_cap(c.N, c.K));
       const ILayout il = ilayout(c.M, c.N, c.K, c.l);
       d.d_off = doff; doff += al4(dl.total);
       d.f_off = foff; foff += al4(fl.total);
@@ -182,20 +221,6 @@ extern "C" int hcran_create(hcran_t *out, const hcran_config *cfgs, int32_t n,
       }
       for (int k = 0; k < c.Ks; k++) db[dl.Psi + k] = min_rate(c.T_s[k], c.lambda_pps[k], c.zbar_bits, c.Bn_hz);
       for (int64_t t = 0; t < int64_t(c.M) * c.K; t++) db[dl.w + t] = c.w ? c.w[t] : 1.0;
-    }
-    // classes in launch order (largest clusters first); longest-processing-time
-    // order inside a class: largest M*N*K*l first
-    h->order.resize(n);
-    std::iota(h->order.begin(), h->order.end(), 0);
-    std::stable_sort(h->order.begin(), h->order.end(), [&](int a, int b) {
-      if (h->cls[a] != h->cls[b]) return h->cls[a] < h->cls[b];
-      const InstDesc &x = h->descs[a], &y = h->descs[b];
-      return int64_t(x.N) * x.M * x.K * x.l > int64_t(y.N) * y.M * y.K * y.l;
-    });
-    for (int k = 0, first = 0; k < kNumClasses; k++) {
-      h->classes[k].csize = class_csize(k);
-      h->classes[k].first = first;
-      first += h->classes[k].count;
     }
     WsLayout &w = h->ws;
     uint64_t o = 0;
@@ -231,14 +256,22 @@ extern "C" int hcran_gain_elems(hcran_t h, int64_t *elems) {
 
 static bool ws_ok(void *ws) { return ws && (reinterpret_cast<uintptr_t>(ws) & 255) == 0; }
 
+// descriptors and launch order -> workspace (stream-ordered)
+static int upload_plan(hcran_t h, char *ws, cudaStream_t st) {
+  if (cudaMemcpyAsync(ws + h->ws.descs, h->descs.data(), sizeof(InstDesc) * h->n, cudaMemcpyHostToDevice,
+                      st) != cudaSuccess ||
+      cudaMemcpyAsync(ws + h->ws.order, h->order.data(), sizeof(int32_t) * h->n, cudaMemcpyHostToDevice,
+                      st) != cudaSuccess)
+    return HCRAN_ECUDA;
+  h->plan_dirty = false;
+  return HCRAN_OK;
+}
+
 extern "C" int hcran_prepare(hcran_t h, void *workspace_dev, void *stream) {
   if (!h || !ws_ok(workspace_dev)) return HCRAN_EINVAL;
   char *ws = static_cast<char *>(workspace_dev);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  if (cudaMemcpyAsync(ws + h->ws.descs, h->descs.data(), sizeof(InstDesc) * h->n,
-                      cudaMemcpyHostToDevice, st) != cudaSuccess ||
-      cudaMemcpyAsync(ws + h->ws.order, h->order.data(), sizeof(int32_t) * h->n,
-                      cudaMemcpyHostToDevice, st) != cudaSuccess ||
+  if (upload_plan(h, ws, st) != HCRAN_OK ||
       cudaMemcpyAsync(ws + h->ws.darena, h->dimage.data(), sizeof(double) * h->dtot,
                       cudaMemcpyHostToDevice, st) != cudaSuccess)
     return HCRAN_ECUDA;
@@ -253,9 +286,7 @@ static int check_tol(const hcran_tol *t) {
   return HCRAN_OK;
 }
 
-static int do_solve(hcran_t h, const float *gains_dev, const hcran_tol *tol, void *workspace_dev,
-                    void *stream) {
-  char *ws = static_cast<char *>(workspace_dev);
+static Tol to_tol(const hcran_tol *tol) {
   Tol t;
   t.tol_dinkelbach = tol->tol_dinkelbach;
   t.tol_scale = tol->tol_scale;
@@ -265,18 +296,32 @@ static int do_solve(hcran_t h, const float *gains_dev, const hcran_tol *tol, voi
   t.max_dual = tol->max_dual;
   t.tie_eps = (float)tol->tie_eps;
   t.q_init = tol->q_init;
+  return t;
+}
+
+// one persistent launch of class L over the first `count` instances of its
+// segment of the order array
+static cudaError_t launch_class(hcran_t h, const LaunchClass &L, const KDims &kd, int csize, int count, int k,
+                                const float *gains_dev, const Tol &t, char *ws, cudaStream_t st, int *launches) {
+  return launch_solve(reinterpret_cast<const InstDesc *>(ws + h->ws.descs),
+                      reinterpret_cast<const int *>(ws + h->ws.order) + L.first, count, gains_dev,
+                      reinterpret_cast<double *>(ws + h->ws.darena), reinterpret_cast<float *>(ws + h->ws.farena),
+                      reinterpret_cast<int *>(ws + h->ws.iarena), reinterpret_cast<InstOut *>(ws + h->ws.outs), t,
+                      kd, csize, reinterpret_cast<int *>(ws + h->ws.counter) + k, st, launches);
+}
+
+static int do_solve(hcran_t h, const float *gains_dev, const hcran_tol *tol, void *workspace_dev,
+                    void *stream) {
+  char *ws = static_cast<char *>(workspace_dev);
+  if (h->plan_dirty && upload_plan(h, ws, static_cast<cudaStream_t>(stream)) != HCRAN_OK) return HCRAN_ECUDA;
+  const Tol t = to_tol(tol);
   int launches = 0;
   cudaError_t err = cudaSuccess;
   for (int k = 0; k < kNumClasses && err == cudaSuccess; k++) {
     const LaunchClass &L = h->classes[k];
     if (L.count == 0) continue;
     int l = 0;
-    err = launch_solve(reinterpret_cast<const InstDesc *>(ws + h->ws.descs),
-                       reinterpret_cast<const int *>(ws + h->ws.order) + L.first, L.count, gains_dev,
-                       reinterpret_cast<double *>(ws + h->ws.darena), reinterpret_cast<float *>(ws + h->ws.farena),
-                       reinterpret_cast<int *>(ws + h->ws.iarena), reinterpret_cast<InstOut *>(ws + h->ws.outs),
-                       t, L.kd, L.csize, reinterpret_cast<int *>(ws + h->ws.counter) + k,
-                       static_cast<cudaStream_t>(stream), &l);
+    err = launch_class(h, L, L.kd, L.csize, L.count, k, gains_dev, t, ws, static_cast<cudaStream_t>(stream), &l);
     launches += l;
   }
   h->last_ws = workspace_dev;
@@ -345,7 +390,7 @@ extern "C" int hcran_get(hcran_t h, int32_t index, hcran_result *out) {
   const char *ws = static_cast<const char *>(h->last_ws);
   const InstDesc &d = h->descs[index];
   const DLayout dl = dlayout(d.M, d.N, d.K, d.Ks, d.l);
-  const FLayout fl = flayout(d.M, d.N, d.K, d.l, d.nchunk);
+  const FLayout fl = flayout(d.M, d.N, d.K, d.l, nchunk_cap(d.N, d.K));
   const ILayout il = ilayout(d.M, d.N, d.K, d.l);
   const char *db = ws + h->ws.darena + sizeof(double) * d.d_off;
   const char *fb = ws + h->ws.farena + sizeof(float) * d.f_off;
@@ -419,6 +464,155 @@ extern "C" int hcran_get_schedule(hcran_t h, int32_t *cluster_size) {
   if (!h || !cluster_size) return HCRAN_EINVAL;
   for (int32_t b = 0; b < h->n; b++)
     cluster_size[b] = h->cls[b] < kNumClasses - 1 ? class_csize(h->cls[b]) : 0;
+  return HCRAN_OK;
+}
+
+extern "C" int hcran_set_schedule(hcran_t h, const int32_t *cluster_size) {
+  if (!h || !cluster_size) return HCRAN_EINVAL;
+  std::vector<int32_t> cls(h->n);
+  for (int32_t b = 0; b < h->n; b++) {
+    const InstDesc &d = h->descs[b];
+    const int C = cluster_size[b];
+    if (C == 0) {
+      cls[b] = kNumClasses - 1;
+      continue;
+    }
+    int k = -1;
+    for (int q = 0; q < kNumClasses - 1; q++)
+      if (class_csize(q) == C) k = q;
+    if (k < 0 || C > d.N) return HCRAN_EINVAL;
+    if (dyn_smem_bytes(resident_kdims(d.M, d.l, d.Ks, d.N, C)) > kMaxDynSmem - kClassMargin) return HCRAN_EINVAL;
+    cls[b] = k;
+  }
+  const std::vector<int32_t> keep = h->cls;
+  h->cls = cls;
+  if (build_classes(h) != 0) {
+    h->cls = keep;
+    build_classes(h);
+    return HCRAN_EINVAL;
+  }
+  return HCRAN_OK;
+}
+
+// Autotuner: for every cluster size in use, time the class's schedule against
+// clusters twice as large on a probe of the class (the first S instances in
+// launch order, S = min(class size, two waves of the current schedule); one
+// Dinkelbach iteration, one SCALE pass, max_dual_probe dual iterations, no
+// early stop) and keep the faster.  A probe over S instances compares
+// throughput when the class fills several waves and latency when it does not.
+extern "C" int hcran_autotune(hcran_t h, const float *gains_dev, const hcran_tol *tol, void *workspace_dev,
+                              void *stream, int32_t max_dual_probe) {
+  if (!h || !gains_dev || !ws_ok(workspace_dev) || (reinterpret_cast<uintptr_t>(gains_dev) & 15) ||
+      max_dual_probe < 1)
+    return HCRAN_EINVAL;
+  int rc = check_tol(tol);
+  if (rc != HCRAN_OK) return rc;
+  char *ws = static_cast<char *>(workspace_dev);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (h->plan_dirty && upload_plan(h, ws, st) != HCRAN_OK) return HCRAN_ECUDA;
+  hcran_tol pt = *tol;
+  pt.tol_dinkelbach = pt.tol_scale = pt.tol_dual = 0.0;
+  pt.max_dinkelbach = 1;
+  pt.max_scale = 1;
+  pt.max_dual = max_dual_probe;
+  const Tol t = to_tol(&pt);
+  int dev = 0, sms = 1;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return HCRAN_ECUDA;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return HCRAN_ECUDA;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return HCRAN_ECUDA;
+  }
+  std::vector<int32_t> cls = h->cls;
+  for (int k = kNumClasses - 2; k >= 1 && rc == HCRAN_OK; k--) {  // cluster sizes 1, 2, 4 (8 has no larger)
+    const LaunchClass L = h->classes[k];
+    if (L.count == 0) continue;
+    const int C = L.csize, C2 = 2 * C;
+    // probe: the first S instances of the class in launch order; every one
+    // of them must have a subcarrier for each CTA of the larger cluster
+    std::vector<int32_t> probe;
+    const int S = std::min(L.count, 2 * (sms / C));
+    for (int i = 0; i < S; i++) probe.push_back(h->order[L.first + i]);
+    bool fits = true;
+    for (int32_t b : probe) fits = fits && h->descs[b].N >= C2;
+    if (!fits) continue;
+    KDims kd1{}, kd2{};
+    for (size_t i = 0; i < probe.size(); i++) {
+      const InstDesc &d = h->descs[probe[i]];
+      const KDims a = resident_kdims(d.M, d.l, d.Ks, d.N, C), b = resident_kdims(d.M, d.l, d.Ks, d.N, C2);
+      if (i == 0) {
+        kd1 = a;
+        kd2 = b;
+      } else {
+        kdims_merge(kd1, a);
+        kdims_merge(kd2, b);
+      }
+    }
+    float ms[2] = {0.f, 0.f};
+    for (int v = 0; v < 2 && rc == HCRAN_OK; v++) {
+      int l = 0;
+      if (cudaEventRecord(e0, st) != cudaSuccess ||
+          launch_class(h, L, v ? kd2 : kd1, v ? C2 : C, (int)probe.size(), k, gains_dev, t, ws, st, &l) !=
+              cudaSuccess ||
+          cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+          cudaEventElapsedTime(&ms[v], e0, e1) != cudaSuccess)
+        rc = HCRAN_ECUDA;
+    }
+    if (rc == HCRAN_OK && ms[1] < ms[0])
+      for (int i = 0; i < L.count; i++) {
+        const int32_t b = h->order[L.first + i];
+        if (h->descs[b].N >= C2) cls[b] = k - 1;
+      }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != HCRAN_OK) return rc;
+  if (cls != h->cls) {
+    h->cls = cls;
+    if (build_classes(h) != 0) return HCRAN_EINVAL;
+  }
+  return HCRAN_OK;
+}
+
+extern "C" int hcran_solve_graph(hcran_t h, const float *gains_dev, const hcran_tol *tol, void *workspace_dev,
+                                 void *stream) {
+  if (!h || !gains_dev || !ws_ok(workspace_dev) || (reinterpret_cast<uintptr_t>(gains_dev) & 15) || !stream)
+    return HCRAN_EINVAL;
+  int rc = check_tol(tol);
+  if (rc != HCRAN_OK) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  char *ws = static_cast<char *>(workspace_dev);
+  if (h->plan_dirty && upload_plan(h, ws, st) != HCRAN_OK) return HCRAN_ECUDA;
+  const bool same = h->graph && h->graph_gains == gains_dev && h->graph_ws == workspace_dev &&
+                    memcmp(&h->graph_tol, tol, sizeof(hcran_tol)) == 0;
+  if (!same) {
+    if (h->graph) {
+      cudaGraphExecDestroy(h->graph);
+      h->graph = nullptr;
+    }
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return HCRAN_ECUDA;
+    rc = do_solve(h, gains_dev, tol, workspace_dev, stream);
+    const cudaError_t ec = cudaStreamEndCapture(st, &g);
+    if (rc != HCRAN_OK || ec != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return HCRAN_ECUDA;
+    }
+    const cudaError_t ei = cudaGraphInstantiate(&h->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) {
+      h->graph = nullptr;
+      return HCRAN_ECUDA;
+    }
+    h->graph_gains = gains_dev;
+    h->graph_ws = workspace_dev;
+    h->graph_tol = *tol;
+  }
+  if (cudaGraphLaunch(h->graph, st) != cudaSuccess) return HCRAN_ECUDA;
+  h->last_ws = workspace_dev;
+  h->last_stream = st;
   return HCRAN_OK;
 }
 

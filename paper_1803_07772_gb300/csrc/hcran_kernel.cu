@@ -196,7 +196,7 @@ __device__ void bind(Ctx &c, const InstDesc &d, const float *gains, double *dare
   c.pmax = db + dl.pmax; c.eta = db + dl.eta; c.mask = db + dl.mask; c.Psi = db + dl.Psi;
   c.w = db + dl.w; c.xi = db + dl.xi; c.zeta = db + dl.zeta; c.zsic = db + dl.zsic;
   c.zsic_next = db + dl.zsic_next;
-  const FLayout fl = flayout(d.M, d.N, d.K, d.l, d.nchunk);
+  const FLayout fl = flayout(d.M, d.N, d.K, d.l, nchunk_cap(d.N, d.K));
   float *fb = farena + d.f_off;
   c.p = fb + fl.p; c.plin = fb + fl.plin; c.pstart = fb + fl.pstart; c.alpha = fb + fl.alpha;
   c.beta = fb + fl.beta; c.pi = fb + fl.pi; c.gam = fb + fl.gam; c.X = fb + fl.X;
@@ -248,6 +248,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       bind(sc, descs[b], gains, darena, farena, iarena);
       sc.csize = csize;
       sc.crank = crank;
+      sc.nchunk = class_nchunk(sc.N, sc.K, csize);  // candidate-utility chunks, a multiple of csize
       sc.n0 = (int)((int64_t)sc.N * crank / csize);
       sc.n1 = (int)((int64_t)sc.N * (crank + 1) / csize);
     }

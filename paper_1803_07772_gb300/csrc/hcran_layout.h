@@ -69,12 +69,26 @@ HCRAN_HD DLayout dlayout(int M, int N, int K, int Ks, int l) {
   return d;
 }
 
+HCRAN_HD int nchunk_for(int N, int K) {
+  int c = kThreads / (K > 0 ? K : 1);
+  if (c < 1) c = 1;
+  if (c > N) c = N;
+  return c;
+}
+// room for candidate-utility chunks in the float arena: enough for any
+// cluster size of the schedule (class_nchunk <= nchunk_cap), so that the
+// arena layout does not depend on the schedule
+HCRAN_HD int nchunk_cap(int N, int K) {
+  const int c = nchunk_for(N, K);
+  return c > 8 ? c : 8;
+}
+
 // float arena of one instance (slot arrays are [n][Up])
 struct FLayout {
   int64_t p, plin, pstart, alpha, beta, pi, gam, X, Aden, Bnum, Cnum, gown, ginv, wslot, slab, SICp, SICm,
       Ptot, cu, cp, cX, ckey, Upart, wf, total;
 };
-HCRAN_HD FLayout flayout(int M, int N, int K, int l, int nchunk) {
+HCRAN_HD FLayout flayout(int M, int N, int K, int l, int nchunk) {  // nchunk: capacity (nchunk_cap)
   FLayout f;
   int64_t o = 0;
   const int64_t L = int64_t(N) * slot_stride(M, l);
@@ -122,12 +136,6 @@ HCRAN_HD ILayout ilayout(int M, int N, int K, int l) {
   return i;
 }
 
-HCRAN_HD int nchunk_for(int N, int K) {
-  int c = kThreads / (K > 0 ? K : 1);
-  if (c < 1) c = 1;
-  if (c > N) c = N;
-  return c;
-}
 
 // per-instance scalar outputs
 struct InstOut {
@@ -267,7 +275,7 @@ inline int pick_class(int M, int l, int Ks, int N) {
 }
 // candidate-utility chunks of an instance solved by clusters of C CTAs: a
 // multiple of C, so that every CTA sums chunks of its own subcarriers
-inline int class_nchunk(int N, int K, int C) {
+HCRAN_HD int class_nchunk(int N, int K, int C) {
   int per = nchunk_for(N, K) / C;
   if (per < 1) per = 1;
   return per * C;

@@ -59,7 +59,8 @@ class Result(C.Structure):
 EXPORTS = ["hcran_create", "hcran_workspace_size", "hcran_gain_elems", "hcran_prepare",
            "hcran_solve", "hcran_solve_host", "hcran_get", "hcran_get_summary",
            "hcran_get_phase_cycles", "hcran_last_launch_count", "hcran_destroy",
-           "hcran_solve_noalloc", "hcran_get_schedule"]
+           "hcran_solve_noalloc", "hcran_get_schedule", "hcran_set_schedule", "hcran_autotune",
+           "hcran_solve_graph"]
 
 
 def load(build_if_missing: bool = True):
@@ -163,6 +164,25 @@ class Solver:
         _check("hcran_solve", self.lib.hcran_solve(
             self.h, C.c_void_p(gains.data_ptr()), C.byref(tol),
             C.c_void_p(self.workspace.data_ptr()), C.c_void_p(self.stream.cuda_stream)))
+
+    def solve_graph(self, gains, tol: Tol):
+        """Same as solve, through a CUDA graph captured on first use for these
+        arguments (the bound stream must be a created stream)."""
+        _check("hcran_solve_graph", self.lib.hcran_solve_graph(
+            self.h, C.c_void_p(gains.data_ptr()), C.byref(tol),
+            C.c_void_p(self.workspace.data_ptr()), C.c_void_p(self.stream.cuda_stream)))
+
+    def set_schedule(self, cluster_size):
+        """Cluster size per instance (1, 2, 4, 8; 0: one CTA streaming from global memory)."""
+        a = np.ascontiguousarray(cluster_size, dtype=np.int32)
+        _check("hcran_set_schedule", self.lib.hcran_set_schedule(self.h, a.ctypes.data_as(_ip)))
+
+    def autotune(self, gains, tol: Tol, max_dual_probe: int = 60) -> np.ndarray:
+        """Time each cluster-size class against clusters twice as large; keep the faster. Returns the schedule."""
+        _check("hcran_autotune", self.lib.hcran_autotune(
+            self.h, C.c_void_p(gains.data_ptr()), C.byref(tol), C.c_void_p(self.workspace.data_ptr()),
+            C.c_void_p(self.stream.cuda_stream), int(max_dual_probe)))
+        return self.schedule()
 
     def solve_host(self, gains_host, tol: Tol):
         """End-to-end solve from host gains; returns (ee, status) host arrays."""

@@ -146,3 +146,30 @@ def test_schedule_picks_smallest_cluster_that_holds_the_state():
         if c > 1:  # the next smaller cluster would not hold the state
             smaller = _res_bytes(inst.M, inst.l, inst.Ks, -(-inst.N // (c // 2)))
             assert smaller > budget - 8 * 1024, (inst.M, inst.N, c, smaller)
+
+
+def test_set_schedule_validates_and_applies():
+    lib = hcran.load()
+    insts = make_workload("batch-4096-uneven", count=6) + make_workload("large-33x1024x512", count=1)
+    made = [_cfg(i) for i in insts]
+    arr = (hcran.Config * len(made))(*[m[0] for m in made])
+    h = C.c_void_p()
+    assert lib.hcran_create(C.byref(h), arr, len(made), None) == 0
+    n = len(insts)
+    get = lambda: (lambda a: (lib.hcran_get_schedule(h, a.ctypes.data_as(hcran._ip)), a)[1])(np.zeros(n, np.int32))
+    base = get()
+    bad = [np.where(np.arange(n) == 0, 3, base),                                   # not a cluster size
+           np.where(np.arange(n) == n - 1, 1, base),                               # 33x1024 state fits no CTA
+           np.array([8 if i.N >= 8 else 1 for i in insts[:-1]] + [0]) * 0 + 16]    # too large a cluster
+    for b in bad:
+        b = np.ascontiguousarray(b, dtype=np.int32)
+        assert lib.hcran_set_schedule(h, b.ctypes.data_as(hcran._ip)) == 1
+        assert np.array_equal(get(), base)
+    assert lib.hcran_set_schedule(h, None) == 1
+    want = np.array([8 if i.N >= 8 else c for i, c in zip(insts[:-1], base[:-1])] + [0], dtype=np.int32)
+    assert lib.hcran_set_schedule(h, want.ctypes.data_as(hcran._ip)) == 0
+    assert np.array_equal(get(), want)
+    everything_streamed = np.zeros(n, np.int32)
+    assert lib.hcran_set_schedule(h, everything_streamed.ctypes.data_as(hcran._ip)) == 0
+    assert np.array_equal(get(), everything_streamed)
+    lib.hcran_destroy(h)

@@ -208,3 +208,68 @@ def test_edge_shapes_match_oracle(shape):
         assert np.array_equal(g["S"], o.S)
         return
     compare_ensemble(inst, g, ensemble(inst, tol), str(shape))
+
+
+def _solver(insts):
+    import torch
+    from paper_1803_07772_gb300 import Solver
+    gains, offs = pack_batch(insts)
+    st = torch.cuda.Stream(device="cuda:0")
+    s = Solver(insts, gain_offsets=offs, device="cuda:0", stream=st)
+    return s, torch.from_numpy(gains).to("cuda:0")
+
+
+def test_graph_replay_matches_direct_launches():
+    from paper_1803_07772_gb300 import make_tol
+    insts = _batch_subset(count=6)
+    s, g = _solver(insts)
+    tol = make_tol(WORKLOADS["batch-4096-uneven"]["tol"], max_dinkelbach=2, max_scale=4)
+    s.solve(g, tol)
+    direct = [s.get(i) for i in range(len(insts))]
+    for _ in range(2):  # capture, then replay
+        s.solve_graph(g, tol)
+        for i, d in enumerate(direct):
+            r = s.get(i)
+            assert r["ee"] == d["ee"] and np.array_equal(r["p"], d["p"]) and np.array_equal(r["S"], d["S"])
+    tol2 = make_tol(WORKLOADS["batch-4096-uneven"]["tol"], max_dinkelbach=1, max_scale=3)
+    s.solve_graph(g, tol2)  # new arguments: re-capture
+    got = [s.get(i)["ee"] for i in range(len(insts))]
+    s.solve(g, tol2)
+    assert got == [s.get(i)["ee"] for i in range(len(insts))]
+
+
+def test_every_cluster_size_matches_oracle_at_fixed_counts():
+    """The same instances forced onto clusters of 1, 2, 4 and 8 CTAs (where
+    the state fits and N allows) and onto the streamed schedule: fixed
+    iteration counts, every selected power held to the strict bar."""
+    insts = _batch_subset(count=3)
+    tol = Tolerances(tol_dinkelbach=0.0, tol_scale=0.0, tol_dual=0.0,
+                     max_dinkelbach=2, max_scale=3, max_dual=40)
+    orcs = [oracle.solve(i, tol) for i in insts]
+    from paper_1803_07772_gb300 import make_tol
+    s, g = _solver(insts)
+    base = s.schedule()
+    for want in [0, 1, 2, 4, 8]:
+        sched = np.array([want if (want == 0 or (want >= b and i.N >= want)) else b
+                          for i, b in zip(insts, base)], np.int32)
+        s.set_schedule(sched)
+        s.solve(g, make_tol(tol, tie_eps=TIE_BAND))
+        for i, (inst, o) in enumerate(zip(insts, orcs)):
+            r = s.get(i)
+            assert r["iters"] == o.iters
+            compare(inst, r, o, "schedule %d (got %d)" % (want, s.schedule()[i]), strict_powers=True)
+
+
+def test_autotuned_schedule_is_valid_and_matches_oracle():
+    from paper_1803_07772_gb300 import make_tol
+    insts = _batch_subset(count=4)
+    s, g = _solver(insts)
+    tol = Tolerances(tol_dinkelbach=0.0, tol_scale=0.0, tol_dual=0.0,
+                     max_dinkelbach=2, max_scale=3, max_dual=40)
+    before = s.schedule()
+    after = s.autotune(g, make_tol(tol, tie_eps=TIE_BAND), max_dual_probe=20)
+    print("schedule before", before, "after autotune", after)
+    assert np.all((after == 0) | (after >= before))
+    s.solve(g, make_tol(tol, tie_eps=TIE_BAND))
+    for i, inst in enumerate(insts):
+        compare(inst, s.get(i), oracle.solve(inst, tol), "autotuned", strict_powers=True)
