@@ -309,16 +309,24 @@ def run_profile_case():
     g = torch.from_numpy(gains).cuda()
     s.solve(g, make_tol(Tolerances(max_dinkelbach=1, max_scale=2, max_dual=100)))
     torch.cuda.synchronize()
+    sched = s.schedule()
     print(json.dumps({"profile_case": WORKLOAD, "instances": 152,
-                      "iters_total": s.summary()["iters"].sum(0).tolist()}))
+                      "iters_total": s.summary()["iters"].sum(0).tolist(),
+                      "schedule": {int(k): int(v) for k, v in zip(*np.unique(sched, return_counts=True))}}))
 
 
-def kernel_hash() -> str:
+# device code of the solve kernel (the host planner and ABI files are left out:
+# they do not change what one launch reads and writes)
+KERNEL_FILES = ("hcran_kernel.cu", "hcran_layout.h", "hcran_dev_common.cuh", "hcran_dev_link.cuh",
+                "hcran_dev_dual.cuh", "hcran_dev_resident.cuh", "hcran_dev_select.cuh")
+
+
+def kernel_hash(read=None) -> str:
     import hashlib
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_1803_07772_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
-        h.update(open(os.path.join(d, f), "rb").read())
+    for f in KERNEL_FILES:
+        h.update(read(f) if read else open(os.path.join(d, f), "rb").read())
     return h.hexdigest()[:16]
 
 

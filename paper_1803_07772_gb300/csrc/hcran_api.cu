@@ -47,8 +47,15 @@ struct hcran_s {
   cudaGraphExec_t graph = nullptr;
   const void *graph_gains = nullptr, *graph_ws = nullptr;
   hcran_tol graph_tol{};
+  // second stream: classes of small clusters run beside those of large ones
+  // and fill the SMs that whole clusters leave free
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
   ~hcran_s() {
     if (graph) cudaGraphExecDestroy(graph);
+    if (side) cudaStreamDestroy(side);
+    if (fork) cudaEventDestroy(fork);
+    if (join) cudaEventDestroy(join);
   }
 };
 
@@ -315,15 +322,29 @@ static int do_solve(hcran_t h, const float *gains_dev, const hcran_tol *tol, voi
   char *ws = static_cast<char *>(workspace_dev);
   if (h->plan_dirty && upload_plan(h, ws, static_cast<cudaStream_t>(stream)) != HCRAN_OK) return HCRAN_ECUDA;
   const Tol t = to_tol(tol);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (!h->side) {
+    if (cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->join, cudaEventDisableTiming) != cudaSuccess)
+      return HCRAN_ECUDA;
+  }
+  // clusters of 8 then 4 on the caller's stream; one CTA, clusters of 2 and
+  // the streamed class on the side stream, forked from and joined back into it
   int launches = 0;
-  cudaError_t err = cudaSuccess;
-  for (int k = 0; k < kNumClasses && err == cudaSuccess; k++) {
+  cudaError_t err = cudaEventRecord(h->fork, st);
+  if (err == cudaSuccess) err = cudaStreamWaitEvent(h->side, h->fork, 0);
+  static const int kOrder[kNumClasses] = {0, 1, 3, 2, 4};
+  for (int i = 0; i < kNumClasses && err == cudaSuccess; i++) {
+    const int k = kOrder[i];
     const LaunchClass &L = h->classes[k];
     if (L.count == 0) continue;
     int l = 0;
-    err = launch_class(h, L, L.kd, L.csize, L.count, k, gains_dev, t, ws, static_cast<cudaStream_t>(stream), &l);
+    err = launch_class(h, L, L.kd, L.csize, L.count, k, gains_dev, t, ws, k <= 1 ? st : h->side, &l);
     launches += l;
   }
+  if (err == cudaSuccess) err = cudaEventRecord(h->join, h->side);
+  if (err == cudaSuccess) err = cudaStreamWaitEvent(st, h->join, 0);
   h->last_ws = workspace_dev;
   h->last_stream = static_cast<cudaStream_t>(stream);
   h->last_launches = launches;

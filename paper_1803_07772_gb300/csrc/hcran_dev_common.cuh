@@ -276,6 +276,13 @@ __device__ __forceinline__ void inst_sync(const Ctx &c) {
   if (c.csize > 1) cooperative_groups::this_cluster().sync();
   else __syncthreads();
 }
+// split cluster barrier: every thread of every CTA arrives, then waits
+__device__ __forceinline__ void cluster_arrive() {
+  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait() {
+  asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
 template <typename T>
 __device__ __forceinline__ T *peer(T *p, int rank) {
   return cooperative_groups::this_cluster().map_shared_rank(p, rank);

@@ -649,13 +649,14 @@ __device__ int dual_loop_res(const Ctx &c, Shared &sh, float *dyn, const KDims &
   int zc = 0;  // generation of the committed SIC multipliers
   stage_link(c, sh, r, szeta, 1.f, zc, gi);
   __syncthreads();
-  stage_rows(c, sh, r, zc ^ 1, gi);
   if (threadIdx.x == 0) cyc[1] += clock64() - t0;
   float dl = 0.f;
   int v = 0;
   for (;;) {
     const long long t1 = clock64();
-    // residual sums at p^v and max |p^v - p^{v-1}| / mask, over the cluster
+    // residual sums at p^v and max |p^v - p^{v-1}| / mask; with a cluster,
+    // the exchange of these per-CTA vectors is a split barrier around the
+    // rows stage (price and SIC sums at p^v), which does not depend on it
     float *xv = (v & 1) ? x.xch1 : x.xch0;
     const int nx = M + 2 * Ks;
     res_partials(c, sh, r, xv, dl);
@@ -664,11 +665,16 @@ __device__ int dual_loop_res(const Ctx &c, Shared &sh, float *dyn, const KDims &
       const float d = warp_max(threadIdx.x < kWarps ? sh.redf[threadIdx.x] : 0.f);
       if (threadIdx.x == 0) xv[nx] = d;
     }
+    if (c.csize > 1) {
+      __syncwarp();
+      cluster_arrive();  // release: this CTA's vector is complete
+    }
+    stage_rows(c, sh, r, zc ^ 1, gi);
     const float *xt = xv;
     if (c.csize > 1) {
-      // peers read this parity's vector before their next barrier; it is
-      // rewritten two iterations later, after that barrier
-      inst_sync(c);
+      // peers read this parity's vector before their next arrival; it is
+      // rewritten two iterations later, after the next wait
+      cluster_wait();
       for (int i = threadIdx.x; i <= nx; i += kThreads) {
         float v[8];
 #pragma unroll
@@ -727,7 +733,6 @@ __device__ int dual_loop_res(const Ctx &c, Shared &sh, float *dyn, const KDims &
     __syncthreads();
     stage_link(c, sh, r, szeta, rsqrtf((float)v + 2.f), zc, gi);
     __syncthreads();
-    stage_rows(c, sh, r, zc ^ 1, gi);
     v++;
     const long long t3 = clock64();
     if (threadIdx.x == 0) {
