@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libhcran.so")
-SOURCES = ["hcran_kernel.cu", "hcran_api.cu", "hcran_noalloc.cu"]
+SOURCES = ["hcran_kernel.cu", "hcran_api.cu", "hcran_noalloc.cu", "mlp_kernels.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC"]
 
@@ -32,6 +32,7 @@ def _stale() -> bool:
     t = os.path.getmtime(LIB)
     deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)]
     deps.append(os.path.join(HERE, "..", "include", "hcran.h"))
+    deps.append(os.path.join(HERE, "..", "include", "hcran_mlp.h"))
     return any(os.path.getmtime(d) > t for d in deps if os.path.exists(d))
 
 

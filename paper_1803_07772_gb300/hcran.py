@@ -61,6 +61,8 @@ EXPORTS = ["hcran_create", "hcran_workspace_size", "hcran_gain_elems", "hcran_pr
            "hcran_get_phase_cycles", "hcran_last_launch_count", "hcran_destroy",
            "hcran_solve_noalloc", "hcran_get_schedule", "hcran_set_schedule", "hcran_autotune",
            "hcran_solve_graph"]
+# include/hcran_mlp.h: tensor-core kernels of the warm-start network
+MLP_EXPORTS = ["hcran_mlp_dense", "hcran_mlp_tc_status"]
 
 
 def load(build_if_missing: bool = True):
@@ -88,6 +90,12 @@ def load(build_if_missing: bool = True):
         "hcran_last_launch_count": ([vp, _ip], C.c_int),
         "hcran_destroy": ([vp], None),
         "hcran_solve_noalloc": ([C.POINTER(Config), vp, C.POINTER(Tol), vp, C.POINTER(Result)], C.c_int),
+        "hcran_get_schedule": ([vp, _ip], C.c_int),
+        "hcran_set_schedule": ([vp, _ip], C.c_int),
+        "hcran_autotune": ([vp, vp, C.POINTER(Tol), vp, vp, C.c_int32], C.c_int),
+        "hcran_solve_graph": ([vp, vp, C.POINTER(Tol), vp, vp], C.c_int),
+        "hcran_mlp_dense": ([vp, vp, vp, vp, C.c_int64, C.c_int32, C.c_int32, C.c_int32, vp, vp], C.c_int),
+        "hcran_mlp_tc_status": ([_ip], C.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)

@@ -14,8 +14,8 @@ from paper_1803_07772_gb300 import hcran
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def declared_functions():
-    src = open(os.path.join(ROOT, "include", "hcran.h")).read()
+def declared_functions(header="hcran.h"):
+    src = open(os.path.join(ROOT, "include", header)).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     return sorted(set(re.findall(r"^\s*(?:int|void)\s+(hcran_\w+)\s*\(", src, flags=re.M)))
 
@@ -27,6 +27,10 @@ def test_library_exports_every_declared_symbol():
     for n in names:
         assert hasattr(lib, n), n
     assert sorted(hcran.EXPORTS) == names
+    mlp = declared_functions("hcran_mlp.h")
+    for n in mlp:
+        assert hasattr(lib, n), n
+    assert sorted(hcran.MLP_EXPORTS) == mlp
 
 
 def _cfg(inst, **over):
