@@ -62,7 +62,9 @@ EXPORTS = ["hcran_create", "hcran_workspace_size", "hcran_gain_elems", "hcran_pr
            "hcran_solve_noalloc", "hcran_get_schedule", "hcran_set_schedule", "hcran_autotune",
            "hcran_solve_graph"]
 # include/hcran_mlp.h: tensor-core kernels of the warm-start network
-MLP_EXPORTS = ["hcran_mlp_dense", "hcran_mlp_tc_status"]
+MLP_EXPORTS = ["hcran_mlp_dense", "hcran_mlp_tc_status", "hcran_mlp_create", "hcran_mlp_destroy",
+               "hcran_mlp_param_count", "hcran_mlp_get_params", "hcran_mlp_set_params", "hcran_mlp_get_grads",
+               "hcran_mlp_forward", "hcran_mlp_loss_grad", "hcran_mlp_backward", "hcran_mlp_adam"]
 
 
 def load(build_if_missing: bool = True):
@@ -96,6 +98,16 @@ def load(build_if_missing: bool = True):
         "hcran_solve_graph": ([vp, vp, C.POINTER(Tol), vp, vp], C.c_int),
         "hcran_mlp_dense": ([vp, vp, vp, vp, C.c_int64, C.c_int32, C.c_int32, C.c_int32, vp, vp], C.c_int),
         "hcran_mlp_tc_status": ([_ip], C.c_int),
+        "hcran_mlp_create": ([C.POINTER(vp), C.c_uint64, C.c_int64], C.c_int),
+        "hcran_mlp_destroy": ([vp], None),
+        "hcran_mlp_param_count": ([vp, _i64p], C.c_int),
+        "hcran_mlp_get_params": ([vp, _fp], C.c_int),
+        "hcran_mlp_set_params": ([vp, _fp], C.c_int),
+        "hcran_mlp_get_grads": ([vp, _fp], C.c_int),
+        "hcran_mlp_forward": ([vp, vp, C.c_int64, vp, vp], C.c_int),
+        "hcran_mlp_loss_grad": ([vp, vp, vp, vp, C.c_int64, C.c_int32, vp, vp], C.c_int),
+        "hcran_mlp_backward": ([vp, vp, C.c_int64, vp], C.c_int),
+        "hcran_mlp_adam": ([vp, C.c_float, C.c_float, C.c_float, C.c_float, vp], C.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
