@@ -193,6 +193,36 @@ int hcran_autotune(hcran_t h, const float *gains_dev, const hcran_tol *tol, void
  * Same results as hcran_solve. */
 int hcran_solve_graph(hcran_t h, const float *gains_dev, const hcran_tol *tol, void *workspace_dev, void *stream);
 
+/* ---- learned warm start ----
+ * The network (include/hcran_mlp.h) reads one row of features per slot of
+ * the cold initial selection (A_k = argmax_m sum_n Gamma, the l strongest
+ * users of A_k's RRH on every subcarrier) and returns one row of outputs per
+ * slot; instance b owns rows [s_off_b, s_off_b + N_b * Up_b), slot (n, u) is
+ * row s_off_b + n * Up_b + u, Up_b = M_b * l_b rounded up to a multiple of 4,
+ * and the instances follow one another in creation order.
+ *   features (BF16, 16 columns, the first four used): (log10 Gamma + 11) / 3,
+ *     rank of Gamma among the K users on (m, n) / K, streaming (0 / 1),
+ *     delay target / 0.1 s; empty slots are all zero;
+ *   outputs (FP32, 16 columns, the first three used): y0 = log(p / mask_m),
+ *     y1 with xi'_m = max(mean of e^y1 over RRH m's slots - 1e-3, 0) /
+ *     (ln2 mask_m), y2 with zeta'_k = mean of e^y2 over user k's slots
+ *     (clipped to [1e-6, 1e6]).
+ * *rows = the number of rows (sum over instances of N * Up). */
+int hcran_warm_rows(hcran_t h, int64_t *rows);
+
+/* Writes the features of every row into features_dev ([rows][16] BF16,
+ * device, 16-byte aligned).  Also leaves the initial selection (A, S) and
+ * its powers in the workspace, where hcran_get reads them (its scalar
+ * results are not updated).  Asynchronous on stream. */
+int hcran_warm_features(hcran_t h, const float *gains_dev, void *workspace_dev, void *stream, void *features_dev);
+
+/* hcran_solve started from the network's outputs (net_out_dev: [rows][16]
+ * FP32, device) instead of the cold point: the same initial selection, p^0
+ * = mask_m e^y0 clipped to [1e-9 mask_m, mask_m], xi' and zeta' as above,
+ * then the C12 projection; E^1 = R(p^0) / P(p^0). */
+int hcran_solve_warm(hcran_t h, const float *gains_dev, const hcran_tol *tol, void *workspace_dev, void *stream,
+                     const float *net_out_dev);
+
 void hcran_destroy(hcran_t h);
 
 /* ---- allocation-free single-instance solve ----------------------------

@@ -17,7 +17,8 @@
 namespace hcran {
 cudaError_t launch_solve(const InstDesc *descs, const int *order, int n_inst, const float *gains,
                          double *darena, float *farena, int *iarena, InstOut *outs, const Tol &tol,
-                         const KDims &kd, int csize, int *counter, cudaStream_t stream, int *launches);
+                         const KDims &kd, int csize, int *counter, cudaStream_t stream, int *launches,
+                         const WarmIO &wio);
 }
 
 using namespace hcran;
@@ -37,6 +38,7 @@ struct hcran_s {
   LaunchClass classes[kNumClasses];
   std::vector<double> dimage;   // full double arena (constants + zeroed multipliers)
   int64_t gain_elems = 0, dtot = 0, ftot = 0, itot = 0;
+  int64_t warm_rows = 0;          // rows of the warm-start feature / output arrays
   WsLayout ws{};
   void *last_ws = nullptr;
   cudaStream_t last_stream = nullptr;
@@ -203,6 +205,7 @@ extern "C" int hcran_create(hcran_t *out, const hcran_config *cfgs, int32_t n,
     if (build_classes(h) != 0) { delete h; return HCRAN_EINVAL; }
     // arenas (sized for any schedule of the instance)
     doff = foff = ioff = 0;
+    int64_t soff = 0;
     for (int32_t b = 0; b < n; b++) {
       const hcran_config &c = cfgs[b];
       InstDesc &d = h->descs[b];
@@ -212,7 +215,9 @@ extern "C" int hcran_create(hcran_t *out, const hcran_config *cfgs, int32_t n,
       d.d_off = doff; doff += al4(dl.total);
       d.f_off = foff; foff += al4(fl.total);
       d.i_off = ioff; ioff += al4(il.total);
+      d.s_off = soff; soff += int64_t(c.N) * slot_stride(c.M, c.l);
     }
+    h->warm_rows = soff;
     h->gain_elems = al4(h->gain_elems);
     h->dtot = doff; h->ftot = foff; h->itot = ioff;
     // constants image of the double arena
@@ -226,7 +231,10 @@ extern "C" int hcran_create(hcran_t *out, const hcran_config *cfgs, int32_t n,
         db[dl.eta + m] = c.eta[m];
         db[dl.mask + m] = c.pmax[m] / c.N;   // spectral mask p^mask = pmax / N
       }
-      for (int k = 0; k < c.Ks; k++) db[dl.Psi + k] = min_rate(c.T_s[k], c.lambda_pps[k], c.zbar_bits, c.Bn_hz);
+      for (int k = 0; k < c.Ks; k++) {
+        db[dl.Psi + k] = min_rate(c.T_s[k], c.lambda_pps[k], c.zbar_bits, c.Bn_hz);
+        db[dl.Tdel + k] = c.T_s[k];
+      }
       for (int64_t t = 0; t < int64_t(c.M) * c.K; t++) db[dl.w + t] = c.w ? c.w[t] : 1.0;
     }
     WsLayout &w = h->ws;
@@ -303,25 +311,28 @@ static Tol to_tol(const hcran_tol *tol) {
   t.max_dual = tol->max_dual;
   t.tie_eps = (float)tol->tie_eps;
   t.q_init = tol->q_init;
+  t.mode = kModeCold;
   return t;
 }
 
 // one persistent launch of class L over the first `count` instances of its
 // segment of the order array
 static cudaError_t launch_class(hcran_t h, const LaunchClass &L, const KDims &kd, int csize, int count, int k,
-                                const float *gains_dev, const Tol &t, char *ws, cudaStream_t st, int *launches) {
+                                const float *gains_dev, const Tol &t, char *ws, cudaStream_t st, int *launches,
+                                const WarmIO &wio = WarmIO{nullptr, nullptr}) {
   return launch_solve(reinterpret_cast<const InstDesc *>(ws + h->ws.descs),
                       reinterpret_cast<const int *>(ws + h->ws.order) + L.first, count, gains_dev,
                       reinterpret_cast<double *>(ws + h->ws.darena), reinterpret_cast<float *>(ws + h->ws.farena),
                       reinterpret_cast<int *>(ws + h->ws.iarena), reinterpret_cast<InstOut *>(ws + h->ws.outs), t,
-                      kd, csize, reinterpret_cast<int *>(ws + h->ws.counter) + k, st, launches);
+                      kd, csize, reinterpret_cast<int *>(ws + h->ws.counter) + k, st, launches, wio);
 }
 
 static int do_solve(hcran_t h, const float *gains_dev, const hcran_tol *tol, void *workspace_dev,
-                    void *stream) {
+                    void *stream, int mode = kModeCold, const WarmIO &wio = WarmIO{nullptr, nullptr}) {
   char *ws = static_cast<char *>(workspace_dev);
   if (h->plan_dirty && upload_plan(h, ws, static_cast<cudaStream_t>(stream)) != HCRAN_OK) return HCRAN_ECUDA;
-  const Tol t = to_tol(tol);
+  Tol t = to_tol(tol);
+  t.mode = mode;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (!h->side) {
     if (cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess ||
@@ -340,7 +351,7 @@ static int do_solve(hcran_t h, const float *gains_dev, const hcran_tol *tol, voi
     const LaunchClass &L = h->classes[k];
     if (L.count == 0) continue;
     int l = 0;
-    err = launch_class(h, L, L.kd, L.csize, L.count, k, gains_dev, t, ws, k <= 1 ? st : h->side, &l);
+    err = launch_class(h, L, L.kd, L.csize, L.count, k, gains_dev, t, ws, k <= 1 ? st : h->side, &l, wio);
     launches += l;
   }
   if (err == cudaSuccess) err = cudaEventRecord(h->join, h->side);
@@ -635,6 +646,32 @@ extern "C" int hcran_solve_graph(hcran_t h, const float *gains_dev, const hcran_
   h->last_ws = workspace_dev;
   h->last_stream = st;
   return HCRAN_OK;
+}
+
+extern "C" int hcran_warm_rows(hcran_t h, int64_t *rows) {
+  if (!h || !rows) return HCRAN_EINVAL;
+  *rows = h->warm_rows;
+  return HCRAN_OK;
+}
+
+extern "C" int hcran_warm_features(hcran_t h, const float *gains_dev, void *workspace_dev, void *stream,
+                                   void *features_dev) {
+  if (!h || !gains_dev || !ws_ok(workspace_dev) || (reinterpret_cast<uintptr_t>(gains_dev) & 15) ||
+      !features_dev || (reinterpret_cast<uintptr_t>(features_dev) & 15))
+    return HCRAN_EINVAL;
+  hcran_tol t{};
+  t.max_dinkelbach = t.max_scale = t.max_dual = 1;
+  return do_solve(h, gains_dev, &t, workspace_dev, stream, kModeFeatures, WarmIO{nullptr, features_dev});
+}
+
+extern "C" int hcran_solve_warm(hcran_t h, const float *gains_dev, const hcran_tol *tol, void *workspace_dev,
+                                void *stream, const float *net_out_dev) {
+  if (!h || !gains_dev || !ws_ok(workspace_dev) || (reinterpret_cast<uintptr_t>(gains_dev) & 15) || !net_out_dev ||
+      (reinterpret_cast<uintptr_t>(net_out_dev) & 15))
+    return HCRAN_EINVAL;
+  const int rc = check_tol(tol);
+  if (rc != HCRAN_OK) return rc;
+  return do_solve(h, gains_dev, tol, workspace_dev, stream, kModeWarm, WarmIO{net_out_dev, nullptr});
 }
 
 extern "C" void hcran_destroy(hcran_t h) { delete h; }

@@ -38,6 +38,10 @@ struct Ctx {
   int *A, *Anew, *S, *uslot;
   float sigma;
   double Pconst;
+  const double *Tdel;  // [Ks] delay targets (warm-start features)
+  int64_t s_off;       // first warm-start row of the instance
+  const float *wout;   // warm-start network outputs (warm mode)
+  void *feat;          // warm-start features (features mode)
 };
 
 struct Shared {

@@ -15,7 +15,7 @@
 // the F(q) test, the R and P sums and the multiplier values that accumulate
 // the subgradient steps.  Reductions run in a fixed order, so results are
 // bit-reproducible run to run.  The pieces live in hcran_dev_*.cuh.
-#include "hcran_dev_select.cuh"
+#include "hcran_dev_warm.cuh"
 
 namespace hcran {
 
@@ -60,6 +60,12 @@ __device__ void solve_instance(const Ctx &c, Shared &sh, float *dyn, const KDims
   long long *cyc = sh.cyc;  // written by thread 0 only
   const long long t_begin = clock64();
   initial_state(c, szeta);
+  if (tol.mode == kModeFeatures) {  // initial selection and the warm-start features only
+    warm_features(c);
+    inst_sync(c);
+    return;
+  }
+  if (tol.mode == kModeWarm) warm_apply(c, sh, szeta);
   double R, P;
   link_all<kLinkOnly>(c, sh, dyn, kd, szeta, 0.f, phase, pending);
   exact_R_P(c, sh, R, P);
@@ -194,6 +200,8 @@ __device__ void bind(Ctx &c, const InstDesc &d, const float *gains, double *dare
   const DLayout dl = dlayout(d.M, d.N, d.K, d.Ks, d.l);
   double *db = darena + d.d_off;
   c.pmax = db + dl.pmax; c.eta = db + dl.eta; c.mask = db + dl.mask; c.Psi = db + dl.Psi;
+  c.Tdel = db + dl.Tdel;
+  c.s_off = d.s_off;
   c.w = db + dl.w; c.xi = db + dl.xi; c.zeta = db + dl.zeta; c.zsic = db + dl.zsic;
   c.zsic_next = db + dl.zsic_next;
   const FLayout fl = flayout(d.M, d.N, d.K, d.l, nchunk_cap(d.N, d.K));
@@ -216,7 +224,7 @@ __device__ void bind(Ctx &c, const InstDesc &d, const float *gains, double *dare
 __global__ void __launch_bounds__(kThreads, 1)
     solve_kernel(const InstDesc *__restrict__ descs, const int *__restrict__ order, int n_inst,
                  const float *__restrict__ gains, double *darena, float *farena, int *iarena,
-                 InstOut *outs, Tol tol, KDims kd, int *counter) {
+                 InstOut *outs, Tol tol, KDims kd, int *counter, WarmIO wio) {
   __shared__ Shared sh;
   __shared__ Ctx sc;
   float *dyn = hcran_dyn;
@@ -249,6 +257,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       sc.csize = csize;
       sc.crank = crank;
       sc.nchunk = class_nchunk(sc.N, sc.K, csize);  // candidate-utility chunks, a multiple of csize
+      sc.wout = wio.out;
+      sc.feat = wio.feat;
       sc.n0 = (int)((int64_t)sc.N * crank / csize);
       sc.n1 = (int)((int64_t)sc.N * (crank + 1) / csize);
     }
@@ -267,7 +277,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 // as many clusters as can be resident at once, capped at n_inst.
 cudaError_t launch_solve(const InstDesc *descs, const int *order, int n_inst, const float *gains,
                          double *darena, float *farena, int *iarena, InstOut *outs, const Tol &tol,
-                         const KDims &kd, int csize, int *counter, cudaStream_t stream, int *launches) {
+                         const KDims &kd, int csize, int *counter, cudaStream_t stream, int *launches,
+                         const WarmIO &wio) {
   *launches = 0;
   if (n_inst <= 0) return cudaSuccess;
   int dev = 0, sms = 0, per_sm = 0;
@@ -305,7 +316,7 @@ cudaError_t launch_solve(const InstDesc *descs, const int *order, int n_inst, co
   err = cudaMemsetAsync(counter, 0, sizeof(int), stream);
   if (err != cudaSuccess) return err;
   err = cudaLaunchKernelEx(&cfg, solve_kernel, descs, order, n_inst, gains, darena, farena, iarena, outs,
-                           tol, kd, counter);
+                           tol, kd, counter, wio);
   if (err != cudaSuccess) return err;
   *launches = 1;
   return cudaGetLastError();

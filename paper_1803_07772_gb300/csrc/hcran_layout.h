@@ -46,11 +46,12 @@ struct InstDesc {
   int64_t i_off;   // element offset in the int arena
   double sigma;    // noise power per subcarrier, N0 * Bn
   double Pconst;   // sum_m (Pc_m + Pf_m)
+  int64_t s_off;   // first row of the instance in the warm-start feature / output arrays
 };
 
 // double arena of one instance
 struct DLayout {
-  int64_t pmax, eta, mask, Psi, w, xi, zeta, zsic, zsic_next, total;
+  int64_t pmax, eta, mask, Psi, Tdel, w, xi, zeta, zsic, zsic_next, total;
 };
 HCRAN_HD DLayout dlayout(int M, int N, int K, int Ks, int l) {
   DLayout d;
@@ -60,6 +61,7 @@ HCRAN_HD DLayout dlayout(int M, int N, int K, int Ks, int l) {
   d.eta = o; o = al4(o + M);
   d.mask = o; o = al4(o + M);
   d.Psi = o; o = al4(o + (Ks > 0 ? Ks : 1));
+  d.Tdel = o; o = al4(o + (Ks > 0 ? Ks : 1));
   d.w = o; o = al4(o + int64_t(M) * K);
   d.xi = o; o = al4(o + M);
   d.zeta = o; o = al4(o + (Ks > 0 ? Ks : 1));
@@ -281,11 +283,25 @@ HCRAN_HD int class_nchunk(int N, int K, int C) {
   return per * C;
 }
 
+// What a launch does with each instance: the whole solve from the cold
+// initial point, only the initial selection and the warm-start features of
+// its slots, or the whole solve from the network's warm start.
+enum SolveMode { kModeCold = 0, kModeFeatures = 1, kModeWarm = 2 };
+
 struct Tol {
   double tol_dinkelbach, tol_scale, tol_dual;
   int32_t max_dinkelbach, max_scale, max_dual;
   float tie_eps;
   double q_init;
+  int32_t mode;  // SolveMode
+};
+
+// warm-start rows (one per slot: row s_off + n * Up + u): the features the
+// features mode writes ([rows][16] BF16) and the network outputs the warm mode
+// reads ([rows][16] FP32)
+struct WarmIO {
+  const float *out;
+  void *feat;
 };
 
 // region offsets (bytes) inside the workspace

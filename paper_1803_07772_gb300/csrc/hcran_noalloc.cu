@@ -22,7 +22,8 @@
 namespace hcran {
 cudaError_t launch_solve(const InstDesc *descs, const int *order, int n_inst, const float *gains,
                          double *darena, float *farena, int *iarena, InstOut *outs, const Tol &tol,
-                         const KDims &kd, int csize, int *counter, cudaStream_t stream, int *launches);
+                         const KDims &kd, int csize, int *counter, cudaStream_t stream, int *launches,
+                         const WarmIO &wio);
 }
 
 using namespace hcran;
@@ -121,6 +122,7 @@ __global__ void noalloc_prep_kernel(double *db, DLayout dl, int M, int N, int K,
   for (int k = threadIdx.x; k < Ks; k += blockDim.x) {
     const double x = tmp[Ks + k] * tmp[k];  // lambda T
     db[dl.Psi + k] = tmp[Ks + k] * zbar / (1.0 + x - sqrt(1.0 + x * x)) / Bn;
+    db[dl.Tdel + k] = tmp[k];
   }
   if (fill_w)
     for (int64_t t = threadIdx.x; t < int64_t(M) * K; t += blockDim.x) db[dl.w + t] = 1.0;
@@ -198,12 +200,13 @@ extern "C" int hcran_solve_noalloc(const hcran_config *cfg, const float *gains_d
   t.max_dual = tol->max_dual;
   t.tie_eps = (float)tol->tie_eps;
   t.q_init = tol->q_init;
+  t.mode = kModeCold;
   int launches = 0;
   if (launch_solve(reinterpret_cast<const InstDesc *>(ws + p.o_desc),
                    reinterpret_cast<const int *>(ws + p.o_order), 1, gains_dev, db,
                    reinterpret_cast<float *>(ws + p.o_farena), reinterpret_cast<int *>(ws + p.o_iarena),
                    reinterpret_cast<InstOut *>(ws + p.o_out), t, p.kd, p.csize,
-                   reinterpret_cast<int *>(ws + p.o_counter), st, &launches) != cudaSuccess)
+                   reinterpret_cast<int *>(ws + p.o_counter), st, &launches, WarmIO{nullptr, nullptr}) != cudaSuccess)
     return HCRAN_ECUDA;
   if (cudaStreamSynchronize(st) != cudaSuccess) return HCRAN_ECUDA;
 

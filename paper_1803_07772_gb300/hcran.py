@@ -60,7 +60,7 @@ EXPORTS = ["hcran_create", "hcran_workspace_size", "hcran_gain_elems", "hcran_pr
            "hcran_solve", "hcran_solve_host", "hcran_get", "hcran_get_summary",
            "hcran_get_phase_cycles", "hcran_last_launch_count", "hcran_destroy",
            "hcran_solve_noalloc", "hcran_get_schedule", "hcran_set_schedule", "hcran_autotune",
-           "hcran_solve_graph"]
+           "hcran_solve_graph", "hcran_warm_rows", "hcran_warm_features", "hcran_solve_warm"]
 # include/hcran_mlp.h: tensor-core kernels of the warm-start network
 MLP_EXPORTS = ["hcran_mlp_dense", "hcran_mlp_tc_status", "hcran_mlp_create", "hcran_mlp_destroy",
                "hcran_mlp_param_count", "hcran_mlp_get_params", "hcran_mlp_set_params", "hcran_mlp_get_grads",
@@ -96,6 +96,9 @@ def load(build_if_missing: bool = True):
         "hcran_set_schedule": ([vp, _ip], C.c_int),
         "hcran_autotune": ([vp, vp, C.POINTER(Tol), vp, vp, C.c_int32], C.c_int),
         "hcran_solve_graph": ([vp, vp, C.POINTER(Tol), vp, vp], C.c_int),
+        "hcran_warm_rows": ([vp, _i64p], C.c_int),
+        "hcran_warm_features": ([vp, vp, vp, vp, vp], C.c_int),
+        "hcran_solve_warm": ([vp, vp, C.POINTER(Tol), vp, vp, vp], C.c_int),
         "hcran_mlp_dense": ([vp, vp, vp, vp, C.c_int64, C.c_int32, C.c_int32, C.c_int32, vp, vp], C.c_int),
         "hcran_mlp_tc_status": ([_ip], C.c_int),
         "hcran_mlp_create": ([C.POINTER(vp), C.c_uint64, C.c_int64], C.c_int),
@@ -203,6 +206,26 @@ class Solver:
             self.h, C.c_void_p(gains.data_ptr()), C.byref(tol), C.c_void_p(self.workspace.data_ptr()),
             C.c_void_p(self.stream.cuda_stream), int(max_dual_probe)))
         return self.schedule()
+
+    def warm_rows(self) -> int:
+        n = C.c_int64()
+        _check("hcran_warm_rows", self.lib.hcran_warm_rows(self.h, C.byref(n)))
+        return n.value
+
+    def warm_features(self, gains, features=None):
+        """Features of every slot of the initial selection ([rows][16] bfloat16 CUDA tensor)."""
+        if features is None:
+            features = self._torch.zeros((self.warm_rows(), 16), dtype=self._torch.bfloat16, device=self.device)
+        _check("hcran_warm_features", self.lib.hcran_warm_features(
+            self.h, C.c_void_p(gains.data_ptr()), C.c_void_p(self.workspace.data_ptr()),
+            C.c_void_p(self.stream.cuda_stream), C.c_void_p(features.data_ptr())))
+        return features
+
+    def solve_warm(self, gains, tol: Tol, net_out):
+        """Solve from the network's outputs ([rows][16] float32 CUDA tensor)."""
+        _check("hcran_solve_warm", self.lib.hcran_solve_warm(
+            self.h, C.c_void_p(gains.data_ptr()), C.byref(tol), C.c_void_p(self.workspace.data_ptr()),
+            C.c_void_p(self.stream.cuda_stream), C.c_void_p(net_out.data_ptr())))
 
     def solve_host(self, gains_host, tol: Tol):
         """End-to-end solve from host gains; returns (ee, status) host arrays."""
