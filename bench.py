@@ -394,6 +394,29 @@ KERNEL_FILES = ("hcran_kernel.cu", "hcran_layout.h", "hcran_dev_common.cuh", "hc
                 "hcran_dev_dual.cuh", "hcran_dev_resident.cuh", "hcran_dev_select.cuh")
 
 
+def run_profile_mlp():
+    """One forward, loss gradient, backward and Adam step of the warm-start
+    network on 2^20 synthetic rows (the profiling case of its kernels)."""
+    import torch
+    from paper_1803_07772_gb300.mlp import MLP
+    T = 1 << 20
+    g = torch.Generator().manual_seed(0)
+    x = torch.zeros((T, 16))
+    x[:, :4] = torch.randn((T, 4), generator=g)
+    x = x.to(torch.bfloat16).cuda()
+    tgt = torch.randn((T, 16), generator=g).cuda()
+    mask = torch.ones((T, 16)).cuda()
+    net = MLP(seed=1, max_rows=T)
+    out = torch.empty((T, 16), dtype=torch.float32, device="cuda")
+    loss = torch.zeros(1, device="cuda")
+    net.forward(x, out)
+    net.loss_grad(out, tgt, mask, loss)
+    net.backward(x)
+    net.adam(1e-3)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_mlp_rows": T, "loss": float(loss.item()), "tc_failed": net.tc_failed()}))
+
+
 def kernel_hash(read=None) -> str:
     import hashlib
     h = hashlib.sha256()
@@ -413,6 +436,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the planner's schedule")
     ap.add_argument("--no-warm", action="store_true", help="skip the learned warm-start leg")
+    ap.add_argument("--profile-mlp", action="store_true",
+                    help="one training step of the warm-start network on 2^20 rows (the case for ncu)")
     ap.add_argument("--warm-train", type=int, default=512, help="training instances of the warm start")
     ap.add_argument("--warm-epochs", type=int, default=8)
     ap.add_argument("--profile-case", action="store_true",
@@ -421,6 +446,9 @@ def main():
     args = ap.parse_args()
     if args.profile_case:
         run_profile_case()
+        return
+    if args.profile_mlp:
+        run_profile_mlp()
         return
     if args.warmup < 3:
         args.warmup = 3

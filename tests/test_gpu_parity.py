@@ -273,3 +273,17 @@ def test_autotuned_schedule_is_valid_and_matches_oracle():
     s.solve(g, make_tol(tol, tie_eps=TIE_BAND))
     for i, inst in enumerate(insts):
         compare(inst, s.get(i), oracle.solve(inst, tol), "autotuned", strict_powers=True)
+
+
+def test_large_instance_matches_oracle_at_fixed_counts():
+    """The 33 x 1024 x 512 shape (l = 4): its dual-loop state (about 24 MB)
+    fits no cluster, so it runs the streamed single-CTA schedule; one
+    Dinkelbach iteration, two SCALE passes of 10 dual iterations, every
+    selected power held to the strict bar."""
+    inst = make_workload("large-33x1024x512", count=1)[0]
+    tol = Tolerances(tol_dinkelbach=0.0, tol_scale=0.0, tol_dual=0.0,
+                     max_dinkelbach=1, max_scale=2, max_dual=10)
+    g = gpu_solve([inst], tol)[0]
+    o = oracle.solve(inst, tol)
+    assert g["iters"] == o.iters
+    compare(inst, g, o, "large fixed-count", strict_powers=True)
