@@ -196,7 +196,7 @@ def run_gpu(args):
         g = torch.from_numpy(gains).to(dev)
     torch.cuda.synchronize(dev)
 
-    # schedule: the planner's smallest-cluster choice, then the autotuner
+    # schedule: the planner's cost-model choice, then the autotuner
     # (untimed); the timed steps replay one CUDA graph of the class launches
     planned = solver.schedule()
     if not args.no_autotune:

@@ -154,16 +154,20 @@ int hcran_get_phase_cycles(hcran_t h, int64_t *cycles);
 int hcran_last_launch_count(hcran_t h, int32_t *launches);
 
 /* Schedule chosen at hcran_create for every instance (no device access):
- * cluster_size[b] = number of CTAs (a thread-block cluster, 1, 2, 4 or 8)
- * that solve instance b with the dual-loop state resident in their shared
- * memory, or 0 when that state does not fit even 8 CTAs and the instance is
- * solved by one CTA streaming each subcarrier's state from global memory.
- * Instances of one cluster size share one persistent launch.  cluster_size:
+ * cluster_size[b] = number of CTAs (a thread-block cluster of 1 to 8) that
+ * solve instance b with the dual-loop state resident in their shared memory,
+ * or 0 when that state does not fit even 8 CTAs and the instance is solved by
+ * one CTA streaming each subcarrier's state from global memory.  Among the
+ * sizes whose state fits, the planner takes the one with the fewest SM
+ * cycles per dual iteration under a cost model measured on GB300 (a CTA's
+ * iteration costs about the same whether it holds a few or up to 512 (n, m)
+ * groups, so fewer, fuller CTAs win).  Instances of one cluster size share one
+ * persistent launch.  cluster_size:
  * caller-owned host array of n int32.  Returns HCRAN_EINVAL on a NULL
  * argument. */
 int hcran_get_schedule(hcran_t h, int32_t *cluster_size);
 
-/* Replace the schedule: cluster_size[b] in {1, 2, 4, 8} (a cluster of that
+/* Replace the schedule: cluster_size[b] in 1 .. 8 (a cluster of that
  * many CTAs with the dual-loop state resident in their shared memory; at
  * least one subcarrier per CTA, and the state must fit) or 0 (one CTA
  * streaming from global memory).  An instance whose class would exceed
@@ -173,11 +177,13 @@ int hcran_get_schedule(hcran_t h, int32_t *cluster_size);
  * size. */
 int hcran_set_schedule(hcran_t h, const int32_t *cluster_size);
 
-/* Autotuner of the schedule.  For each cluster size in use (1, 2, 4) it times
- * that class's launch against clusters twice as large on the class's first
+/* Autotuner of the schedule.  For each cluster size C < 8 in use it times
+ * that class's launch against clusters of min(2 C, 8) CTAs on the class's first
  * S instances in launch order (S = the class size, at most two waves of the
  * current schedule), with one Dinkelbach iteration, one SCALE pass and
- * exactly max_dual_probe dual iterations, and keeps the faster schedule.
+ * exactly max(max_dual_probe / 4, 1) and that plus max_dual_probe dual
+ * iterations, and keeps the schedule whose extra max_dual_probe dual
+ * iterations take less time (the dual loop is almost all of a full solve).
  * Probes overwrite the solution state in the workspace (a later solve starts
  * afresh).  Synchronises the stream.  gains_dev and workspace as for
  * hcran_solve; tol supplies tie_eps and q_init.  Returns HCRAN_EINVAL on bad

@@ -340,18 +340,22 @@ static int do_solve(hcran_t h, const float *gains_dev, const hcran_tol *tol, voi
         cudaEventCreateWithFlags(&h->join, cudaEventDisableTiming) != cudaSuccess)
       return HCRAN_ECUDA;
   }
-  // clusters of 8 then 4 on the caller's stream; one CTA, clusters of 2 and
-  // the streamed class on the side stream, forked from and joined back into it
+  // clusters of 8 down to 4 CTAs on the caller's stream; single CTAs, then
+  // clusters of 2 and 3, then the streamed class on a side stream forked from
+  // and joined back into it, so that they fill the SMs the large clusters
+  // leave free
   int launches = 0;
   cudaError_t err = cudaEventRecord(h->fork, st);
   if (err == cudaSuccess) err = cudaStreamWaitEvent(h->side, h->fork, 0);
-  static const int kOrder[kNumClasses] = {0, 1, 3, 2, 4};
+  static const int kOrder[kNumClasses] = {class_of(8), class_of(7), class_of(6), class_of(5), class_of(4),
+                                          class_of(1), class_of(2), class_of(3), kNumClasses - 1};
   for (int i = 0; i < kNumClasses && err == cudaSuccess; i++) {
     const int k = kOrder[i];
     const LaunchClass &L = h->classes[k];
     if (L.count == 0) continue;
     int l = 0;
-    err = launch_class(h, L, L.kd, L.csize, L.count, k, gains_dev, t, ws, k <= 1 ? st : h->side, &l, wio);
+    const bool on_main = k < kNumClasses - 1 && L.csize >= 4;
+    err = launch_class(h, L, L.kd, L.csize, L.count, k, gains_dev, t, ws, on_main ? st : h->side, &l, wio);
     launches += l;
   }
   if (err == cudaSuccess) err = cudaEventRecord(h->join, h->side);
@@ -526,12 +530,17 @@ extern "C" int hcran_set_schedule(hcran_t h, const int32_t *cluster_size) {
   return HCRAN_OK;
 }
 
-// Autotuner: for every cluster size in use, time the class's schedule against
-// clusters twice as large on a probe of the class (the first S instances in
-// launch order, S = min(class size, two waves of the current schedule); one
-// Dinkelbach iteration, one SCALE pass, max_dual_probe dual iterations, no
-// early stop) and keep the faster.  A probe over S instances compares
-// throughput when the class fills several waves and latency when it does not.
+// Autotuner: for every cluster size C < 8 in use, time the class's schedule
+// against clusters of min(2 C, 8) CTAs on a probe of the class (the first S
+// instances in launch order, S = min(class size, two waves of the current
+// schedule); one Dinkelbach iteration, one SCALE pass, no early stop) and
+// keep the faster.  Each schedule is timed twice, with max_dual_probe / 4 and
+// with max_dual_probe dual iterations, and compared on the difference: the
+// cost of the dual iterations alone, which make up almost all of a full solve,
+// without the selection and set-up of the probe's single Dinkelbach
+// iteration, which would otherwise dominate it.  A probe over S instances
+// compares throughput when the class fills several waves and latency when it
+// does not.
 extern "C" int hcran_autotune(hcran_t h, const float *gains_dev, const hcran_tol *tol, void *workspace_dev,
                               void *stream, int32_t max_dual_probe) {
   if (!h || !gains_dev || !ws_ok(workspace_dev) || (reinterpret_cast<uintptr_t>(gains_dev) & 15) ||
@@ -546,8 +555,11 @@ extern "C" int hcran_autotune(hcran_t h, const float *gains_dev, const hcran_tol
   pt.tol_dinkelbach = pt.tol_scale = pt.tol_dual = 0.0;
   pt.max_dinkelbach = 1;
   pt.max_scale = 1;
-  pt.max_dual = max_dual_probe;
-  const Tol t = to_tol(&pt);
+  const int V1 = max_dual_probe / 4 > 0 ? max_dual_probe / 4 : 1, V2 = V1 + max_dual_probe;
+  pt.max_dual = V1;
+  const Tol t1 = to_tol(&pt);
+  pt.max_dual = V2;
+  const Tol t2 = to_tol(&pt);
   int dev = 0, sms = 1;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return HCRAN_ECUDA;
@@ -558,10 +570,10 @@ extern "C" int hcran_autotune(hcran_t h, const float *gains_dev, const hcran_tol
     return HCRAN_ECUDA;
   }
   std::vector<int32_t> cls = h->cls;
-  for (int k = kNumClasses - 2; k >= 1 && rc == HCRAN_OK; k--) {  // cluster sizes 1, 2, 4 (8 has no larger)
+  for (int k = kNumClasses - 2; k >= 1 && rc == HCRAN_OK; k--) {  // cluster sizes 1 .. 7 (8 has no larger)
     const LaunchClass L = h->classes[k];
     if (L.count == 0) continue;
-    const int C = L.csize, C2 = 2 * C;
+    const int C = L.csize, C2 = 2 * C < kMaxCluster ? 2 * C : kMaxCluster;
     // probe: the first S instances of the class in launch order; every one
     // of them must have a subcarrier for each CTA of the larger cluster
     std::vector<int32_t> probe;
@@ -582,20 +594,21 @@ extern "C" int hcran_autotune(hcran_t h, const float *gains_dev, const hcran_tol
         kdims_merge(kd2, b);
       }
     }
-    float ms[2] = {0.f, 0.f};
-    for (int v = 0; v < 2 && rc == HCRAN_OK; v++) {
-      int l = 0;
-      if (cudaEventRecord(e0, st) != cudaSuccess ||
-          launch_class(h, L, v ? kd2 : kd1, v ? C2 : C, (int)probe.size(), k, gains_dev, t, ws, st, &l) !=
-              cudaSuccess ||
-          cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
-          cudaEventElapsedTime(&ms[v], e0, e1) != cudaSuccess)
-        rc = HCRAN_ECUDA;
-    }
-    if (rc == HCRAN_OK && ms[1] < ms[0])
+    float ms[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
+    for (int v = 0; v < 2 && rc == HCRAN_OK; v++)
+      for (int j = 0; j < 2 && rc == HCRAN_OK; j++) {
+        int l = 0;
+        if (cudaEventRecord(e0, st) != cudaSuccess ||
+            launch_class(h, L, v ? kd2 : kd1, v ? C2 : C, (int)probe.size(), k, gains_dev, j ? t2 : t1, ws, st,
+                         &l) != cudaSuccess ||
+            cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(&ms[v][j], e0, e1) != cudaSuccess)
+          rc = HCRAN_ECUDA;
+      }
+    if (rc == HCRAN_OK && ms[1][1] - ms[1][0] < ms[0][1] - ms[0][0])
       for (int i = 0; i < L.count; i++) {
         const int32_t b = h->order[L.first + i];
-        if (h->descs[b].N >= C2) cls[b] = k - 1;
+        if (h->descs[b].N >= C2) cls[b] = class_of(C2);
       }
   }
   cudaEventDestroy(e0);

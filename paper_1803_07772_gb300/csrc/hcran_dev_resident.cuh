@@ -7,18 +7,19 @@
 // memory only, and the powers, the committed multipliers and xi', zeta' go
 // back to global memory at the end.
 //
-// One iteration is four block-wide stages, each over a flat index space so
+// One iteration is three block-wide stages, each over a flat index space so
 // that every thread has work and long independent loops:
+//   sums    per (n, j): the prices a transmitter of RRH j pays towards the
+//           other RRHs' users (row j of the slab against pi) and the SIC+ /
+//           SIC- sums of row j over the nonzero SIC multipliers of n; beside
+//           them, on the last warps, the residual sums over n (RRH totals,
+//           streaming rates) and the projected subgradient steps of xi'
+//           (C12) and zeta' (C13-hat) they give
 //   power   per (n, m): closed-form KKT power of the l slots of RRH m on n
 //           (eq. 653 / 683, log-power variable, Jacobi) and the RRH total
 //   link    per (n, m): interference, SINR and victim prices of the l slots,
 //           the streaming-rate contributions, and the step of the SIC
 //           multipliers of (n, m) (C14 in divided form)
-//   rows    per (n, j): the prices a transmitter of RRH j pays towards the
-//           other RRHs' users (row j of the slab against pi) and the SIC+ /
-//           SIC- sums of row j over the nonzero SIC multipliers of n
-//   update  per RRH and per streaming user: the residual sums over n and the
-//           projected subgradient steps of xi' (C12) and zeta' (C13-hat)
 // The SIC multipliers are unevaluated float pairs (hi + lo): about 48
 // significant bits through the accumulated steps, with no FP64 arithmetic in
 // the stages.  Every sum runs in a fixed order, so results are reproducible.
@@ -39,11 +40,10 @@ struct RView {
 };
 
 struct RScratch {
-  float *xch0, *xch1;  // per-CTA partial sums, by iteration parity
-  float *xtot;         // their totals over the cluster
+  float *xch0, *xch1;  // the CTA's residual vector, by iteration parity
   float *xih, *xil;    // xi' as (hi, lo) float pairs
   float *lzh, *lzl;    // log2 zeta' as (hi, lo) float pairs
-  float *pmf, *xscale, *psi;  // pmax_m, 1 / (ln2 mask_m), Psi_k
+  float *pmf, *xsp, *psi;  // pmax_m, 1 / (ln2 mask_m pmax_m), Psi_k
 };
 
 __device__ __forceinline__ RScratch res_scratch(const KDims &kd) {
@@ -52,8 +52,7 @@ __device__ __forceinline__ RScratch res_scratch(const KDims &kd) {
   RScratch s;
   s.xch0 = b;
   s.xch1 = b + xf;
-  s.xtot = b + 2 * xf;
-  b += 3 * xf;
+  b += 2 * xf;
   const int m4 = (int)al4(kd.Mmax), s4 = (int)al4(kd.KSmax > 0 ? kd.KSmax : 1);
   s.xih = b;
   s.xil = b + m4;
@@ -62,9 +61,9 @@ __device__ __forceinline__ RScratch res_scratch(const KDims &kd) {
   s.lzl = b + s4;
   b += 2 * s4;
   s.pmf = b;
-  b += al4(kd.Mmax);
-  s.xscale = b;
-  b += al4(kd.Mmax);
+  b += m4;
+  s.xsp = b;
+  b += m4;
   s.psi = b;
   return s;
 }
@@ -225,9 +224,46 @@ __device__ __forceinline__ void stage_totals(const Ctx &c, const RGeom &gm, cons
   }
 }
 
+// Projected subgradient steps from the residual sums of the last point:
+//   xi'_m        += delta (sum_n P_{m,n} - pmax_m) / (ln2 mask_m pmax_m), then [.]+
+//   log2 zeta'_k += clip((Psi_k - r_k) / max(sum_n alpha, 0.05), -1, 1), clipped
+// (C12 and C13-hat; the zeta' step is multiplicative, a sum in log2 scale),
+// accumulated in (hi, lo) float pairs.  The new xi'_m goes to sh.xif, the
+// new zeta'_k to szeta.
+__device__ __forceinline__ void xi_update(const RScratch &x, Shared &sh, int m, float tot, float delta) {
+  const float step = delta * (tot - x.pmf[m]) * x.xsp[m];
+  float hi = x.xih[m], lo = x.xil[m];
+  if (hi != 0.f || step > 0.f) {  // stays exactly 0 while the constraint is slack
+    ff_add(hi, lo, step);
+    if (!(hi > 0.f)) {
+      hi = 0.f;
+      lo = 0.f;
+    }
+    x.xih[m] = hi;
+    x.xil[m] = lo;
+  }
+  sh.xif[m] = hi;
+}
+__device__ __forceinline__ void zeta_update(const RScratch &x, float *szeta, int ks, float rr, float as) {
+  const float e = fminf(fmaxf((x.psi[ks] - rr) / fmaxf(as, (float)kZetaAsumMin), -1.f), 1.f);
+  float hi = x.lzh[ks], lo = x.lzl[ks];
+  ff_add(hi, lo, e);
+  if (hi < kLog2ZetaMin) {
+    hi = kLog2ZetaMin;
+    lo = 0.f;
+  } else if (hi > kLog2ZetaMax) {
+    hi = kLog2ZetaMax;
+    lo = 0.f;
+  }
+  x.lzh[ks] = hi;
+  x.lzl[ks] = lo;
+  szeta[ks] = exp2f(hi) * (1.f + lo * LN2F);
+}
+
 // KKT power of one slot (eq. 653 / 683): den = [elastic] q eta_m + xi'_m +
 // prices paid towards other RRHs' users + weaker users of (m, n) + SIC+;
-// num = c w alpha / ln2 + SIC- p_lin; p = clip(num / den, p_floor, mask)
+// num = c w alpha / ln2 + SIC- p_lin with c = 1 (elastic) or zeta'_k;
+// p = clip(num / den, p_floor, mask)
 struct PowerCtx {
   float PIO, SP, SM, qe, xf, mk, fl, im;
   int Ke;
@@ -274,6 +310,17 @@ __device__ __forceinline__ float power_group(const RView &r, const PowerCtx &q, 
   return tot;
 }
 
+__device__ __forceinline__ void power_ctx(PowerCtx &q, const Shared &sh, const RView &r, int h, int m) {
+  q.PIO = r.pio[h];
+  q.SP = r.Sp[h];
+  q.SM = r.Sm[h];
+  q.qe = sh.qeta[m];
+  q.xf = sh.xif[m];
+  q.mk = sh.maskf[m];
+  q.fl = sh.floorf[m];
+  q.im = sh.invmask[m];
+}
+
 template <int L>
 __device__ __forceinline__ float power_stage_l(const Ctx &c, const Shared &sh, const RView &r, const float *szeta,
                                                const GIt &gi) {
@@ -283,23 +330,15 @@ __device__ __forceinline__ float power_stage_l(const Ctx &c, const Shared &sh, c
   float dmax = 0.f;
   int t = gi.t0, m = gi.m0;
   for (int h = threadIdx.x; h < G; h += kThreads, group_next(gi, M, t, m)) {
-    const int base = t * Up + m * L;
-    q.PIO = r.pio[h];
-    q.SP = r.Sp[h];
-    q.SM = r.Sm[h];
-    q.qe = sh.qeta[m];
-    q.xf = sh.xif[m];
-    q.mk = sh.maskf[m];
-    q.fl = sh.floorf[m];
-    q.im = sh.invmask[m];
-    r.Pt[h] = power_group<L>(r, q, szeta, base, dmax);
+    power_ctx(q, sh, r, h, m);
+    r.Pt[h] = power_group<L>(r, q, szeta, t * Up + m * L, dmax);
     clear_sub(c, r, t, m);
   }
   return dmax;
 }
 
 // power stage: KKT power of the l slots of (n, m) from the sums of the last
-// link / rows stages and the current multipliers; RRH total at the new point.
+// link / sums stages and the current multipliers; RRH total at the new point.
 // Returns the thread's max |p_new - p| / mask.
 __device__ __forceinline__ float stage_power(const Ctx &c, const Shared &sh, const RGeom &gm, const float *szeta,
                                              const GIt &gi) {
@@ -318,14 +357,7 @@ __device__ __forceinline__ float stage_power(const Ctx &c, const Shared &sh, con
   int t = gi.t0, m = gi.m0;
   for (int h = threadIdx.x; h < G; h += kThreads, group_next(gi, M, t, m)) {
     const int base = t * Up + m * l;
-    q.PIO = r.pio[h];
-    q.SP = r.Sp[h];
-    q.SM = r.Sm[h];
-    q.qe = sh.qeta[m];
-    q.xf = sh.xif[m];
-    q.mk = sh.maskf[m];
-    q.fl = sh.floorf[m];
-    q.im = sh.invmask[m];
+    power_ctx(q, sh, r, h, m);
     float tot = 0.f, own = 0.f;
     for (int s = l - 1; s >= 0; s--) {
       const int e = base + s;
@@ -576,10 +608,12 @@ __device__ __forceinline__ void stage_rows(const Ctx &c, const Shared &sh, const
 // this CTA's residual sums over its subcarriers into xv: RRH totals [M],
 // streaming rates [Ks], streaming alphas [Ks].  Teams of 8 lanes, one sum per
 // team, lanes over the subcarriers and a 3-step shuffle tree (fixed order).
-// The warp's max |dp| / mask goes to sh.redf.
-__device__ __forceinline__ void res_partials(const Ctx &c, Shared &sh, const RGeom &gm, float *xv, float dl) {
+// Warps take the sums from the last warp down (the sums stage hands its (n, j)
+// rows out from the first thread up): the last res_warps(nq) warps hold work.
+__device__ __forceinline__ int res_warps(int nq) { return nq >= 4 * kWarps ? kWarps : (nq + 3) / 4; }
+__device__ __forceinline__ void res_partials(const Ctx &c, const RGeom &gm, float *xv) {
   const RView r = res_view(c, gm);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, sub = lane & 7;
+  const int warp = kWarps - 1 - (int)(threadIdx.x >> 5), lane = threadIdx.x & 31, sub = lane & 7;
   const int M = c.M, Ks = c.Ks, nq = M + 2 * Ks, Nc = r.Nc;
   for (int q0 = warp * 4; q0 < nq; q0 += kThreads / 8) {  // warp-uniform trip count
     const int q = q0 + (lane >> 3);
@@ -611,30 +645,34 @@ __device__ __forceinline__ void res_partials(const Ctx &c, Shared &sh, const RGe
     a += __shfl_xor_sync(0xffffffffu, a, 1);
     if (sub == 0 && q < nq) xv[q] = a;
   }
-  dl = warp_max(dl);
-  if (lane == 0) sh.redf[warp] = dl;
 }
 
 // One dual loop of Algorithm 1 (one SCALE pass) on resident state.  Same
 // iteration as dual_loop: link at p^0 (SIC step delta_0 = 1); then per
-// iteration the stop test on max |p^v - p^{v-1}| / mask, the projected
-// subgradient step on xi' and zeta' from the residuals at p^v, the KKT power
-// p^{v+1} and the link / rows stages at p^{v+1}.  Returns the iterations run.
+// iteration the stop test on max |p^v - p^{v-1}| / mask, the residual sums at
+// p^v with the steps of xi' and zeta' they give (beside the price and SIC
+// sums), the KKT power p^{v+1} and the link stage at p^{v+1}.  Returns the
+// iterations run.
 __device__ int dual_loop_res(const Ctx &c, Shared &sh, float *dyn, const KDims &kd, float *szeta,
                              const Tol &tol, long long *cyc, unsigned &phase, unsigned &pending) {
   const int Vmax = tol.max_dual > 0 ? tol.max_dual : 1;
-  const int M = c.M, Ks = c.Ks;
+  const int M = c.M, Ks = c.Ks, nq = M + 2 * Ks;
   const RGeom r = res_geom(c, kd);
   const RScratch x = res_scratch(kd);
   const long long t0 = clock64();
   const GIt gi = group_iter(M);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // the residual sums run on the last P warps; their thread u (counted from
+  // the first of them) takes the step of xi'_u (u < M) or zeta'_{u-M}
+  const int P = res_warps(nq);
+  const int u = (int)threadIdx.x - (kWarps - P) * 32;
   load_res(c, r, c.n0);
   for (int m = threadIdx.x; m < M; m += kThreads) {
     const float hi = (float)c.xi[m];
     x.xih[m] = hi;
     x.xil[m] = (float)(c.xi[m] - (double)hi);
     x.pmf[m] = (float)c.pmax[m];
-    x.xscale[m] = 1.f / (LN2F * sh.maskf[m]);
+    x.xsp[m] = (float)(1.0 / (LN2D * c.mask[m] * c.pmax[m]));
   }
   for (int k = threadIdx.x; k < Ks; k += kThreads) {
     const double lz = log2(c.zeta[k]);
@@ -643,6 +681,7 @@ __device__ int dual_loop_res(const Ctx &c, Shared &sh, float *dyn, const KDims &
     x.lzl[k] = (float)(lz - (double)hi);
     x.psi[k] = sh_psi(c, k);
   }
+  if (threadIdx.x < kWarps) sh.redf[threadIdx.x] = 0.f;
   __syncthreads();
   stage_totals(c, r, gi);
   __syncthreads();
@@ -650,86 +689,75 @@ __device__ int dual_loop_res(const Ctx &c, Shared &sh, float *dyn, const KDims &
   stage_link(c, sh, r, szeta, 1.f, zc, gi);
   __syncthreads();
   if (threadIdx.x == 0) cyc[1] += clock64() - t0;
-  float dl = 0.f;
   int v = 0;
   for (;;) {
     const long long t1 = clock64();
-    // residual sums at p^v and max |p^v - p^{v-1}| / mask; with a cluster,
-    // the exchange of these per-CTA vectors is a split barrier around the
-    // rows stage (price and SIC sums at p^v), which does not depend on it
-    float *xv = (v & 1) ? x.xch1 : x.xch0;
-    const int nx = M + 2 * Ks;
-    res_partials(c, sh, r, xv, dl);
-    __syncthreads();
-    if (threadIdx.x < 32) {
-      const float d = warp_max(threadIdx.x < kWarps ? sh.redf[threadIdx.x] : 0.f);
-      if (threadIdx.x == 0) xv[nx] = d;
-    }
-    if (c.csize > 1) {
-      __syncwarp();
-      cluster_arrive();  // release: this CTA's vector is complete
-    }
-    stage_rows(c, sh, r, zc ^ 1, gi);
-    const float *xt = xv;
-    if (c.csize > 1) {
-      // peers read this parity's vector before their next arrival; it is
-      // rewritten two iterations later, after the next wait
-      cluster_wait();
-      for (int i = threadIdx.x; i <= nx; i += kThreads) {
-        float v[8];
-#pragma unroll
-        for (int q = 0; q < 8; q++) v[q] = q < c.csize ? peer(xv, q)[i] : 0.f;
-        float t = v[0];
-#pragma unroll
-        for (int q = 1; q < 8; q++)
-          if (q < c.csize) t = i < nx ? t + v[q] : fmaxf(t, v[q]);
-        x.xtot[i] = t;
-      }
-      xt = x.xtot;
-    }
-    __syncthreads();
-    const float d = xt[nx];
-    if ((v > 0 && d < (float)tol.tol_dual) || v >= Vmax) break;
-    // projected subgradient steps in FP32, accumulated in (hi, lo) float
-    // pairs: xi' on threads 0 .. M-1 (M <= kMaxM), zeta' (in log2 scale, where
-    // the multiplicative step of C13-hat is a sum) on threads kMaxM and up
+    // max |p^v - p^{v-1}| / mask over this CTA, from the warps' maxima of the
+    // last power stage (0 before the first)
+    const float dloc = warp_max(lane < kWarps ? sh.redf[lane] : 0.f);
     const float delta = rsqrtf((float)v + 1.f);
-    if (threadIdx.x < M) {
-      const int m = threadIdx.x;
-      const float pm = x.pmf[m];
-      const float step = delta * ((xt[m] - pm) / pm) * x.xscale[m];
-      float hi = x.xih[m], lo = x.xil[m];
-      if (hi != 0.f || step > 0.f) {
-        ff_add(hi, lo, step);
-        if (!(hi > 0.f)) {
-          hi = 0.f;
-          lo = 0.f;
+    if (c.csize == 1) {
+      if ((v > 0 && dloc < (float)tol.tol_dual) || v >= Vmax) break;
+      if (u >= 0) {  // residual sums, then the multiplier steps they give
+        res_partials(c, r, x.xch0);
+        asm volatile("bar.sync 1, %0;" ::"r"(P * 32) : "memory");
+        if (u < M) xi_update(x, sh, u, x.xch0[u], delta);
+        else if (u < M + Ks) zeta_update(x, szeta, u - M, x.xch0[u], x.xch0[u + Ks]);
+        for (int ks = u - M + P * 32; ks < Ks; ks += P * 32)
+          zeta_update(x, szeta, ks, x.xch0[M + ks], x.xch0[M + Ks + ks]);
+      }
+      stage_rows(c, sh, r, zc ^ 1, gi);
+      __syncthreads();
+    } else {
+      // the per-CTA residual vectors (and maxima) are exchanged through a
+      // split cluster barrier around the price and SIC sums, which do not
+      // depend on them; peers read this parity's vector before their next
+      // arrival, and it is rewritten two iterations later, after the next wait
+      float *xv = (v & 1) ? x.xch1 : x.xch0;
+      const int C = c.csize;
+      if (u >= 0) res_partials(c, r, xv);
+      if (threadIdx.x == kThreads - 1) xv[nq] = dloc;
+      __syncwarp();
+      cluster_arrive();  // release: this thread's part of the vector is written
+      stage_rows(c, sh, r, zc ^ 1, gi);
+      cluster_wait();
+      // every load of a peer's vector is issued before the first is used
+      float dv[8];
+#pragma unroll
+      for (int q = 0; q < 8; q++) dv[q] = q < C ? peer(xv, q)[nq] : 0.f;
+      float d = dloc;
+#pragma unroll
+      for (int q = 0; q < 8; q++) d = fmaxf(d, dv[q]);
+      const bool stop = (v > 0 && d < (float)tol.tol_dual) || v >= Vmax;
+      if (!stop) {  // cluster totals in rank order, then the steps
+        for (int i = threadIdx.x; i < M + Ks; i += kThreads) {
+          const bool z = i >= M;
+          float a[8], b[8];
+#pragma unroll
+          for (int q = 0; q < 8; q++) {
+            const float *pv = q < C ? peer(xv, q) : xv;
+            a[q] = q < C ? pv[i] : 0.f;
+            b[q] = q < C && z ? pv[i + Ks] : 0.f;
+          }
+          float t = a[0], t2 = b[0];
+#pragma unroll
+          for (int q = 1; q < 8; q++)
+            if (q < C) {
+              t += a[q];
+              t2 += b[q];
+            }
+          if (!z) xi_update(x, sh, i, t, delta);
+          else zeta_update(x, szeta, i - M, t, t2);
         }
-        x.xih[m] = hi;
-        x.xil[m] = lo;
       }
-      sh.xif[m] = hi;
+      __syncthreads();
+      if (stop) break;
     }
-    for (int ks = (int)threadIdx.x - kMaxM; ks >= 0 && ks < Ks; ks += kThreads - kMaxM) {
-      const float rr = xt[M + ks], as = xt[M + Ks + ks];
-      const float e = fminf(fmaxf((x.psi[ks] - rr) / fmaxf(as, (float)kZetaAsumMin), -1.f), 1.f);
-      float hi = x.lzh[ks], lo = x.lzl[ks];
-      ff_add(hi, lo, e);
-      if (hi < kLog2ZetaMin) {
-        hi = kLog2ZetaMin;
-        lo = 0.f;
-      } else if (hi > kLog2ZetaMax) {
-        hi = kLog2ZetaMax;
-        lo = 0.f;
-      }
-      x.lzh[ks] = hi;
-      x.lzl[ks] = lo;
-      szeta[ks] = exp2f(hi) * (1.f + lo * LN2F);
-    }
-    __syncthreads();
     const long long t2 = clock64();
     zc ^= 1;  // the multipliers of the last link stage become the committed ones
-    dl = stage_power(c, sh, r, szeta, gi);
+    float dl = stage_power(c, sh, r, szeta, gi);
+    dl = warp_max(dl);
+    if (lane == 0) sh.redf[warp] = dl;
     __syncthreads();
     stage_link(c, sh, r, szeta, rsqrtf((float)v + 2.f), zc, gi);
     __syncthreads();

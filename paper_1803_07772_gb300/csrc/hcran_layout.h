@@ -193,16 +193,16 @@ HCRAN_HD int64_t res_floats(int M, int l, int Ks, int Nc) {
          4 * al4(int64_t(Nc) * M) + 4 * al4(int64_t(Nc) * Mi) + al4(int64_t(Nc) * NW) +
          2 * al4(int64_t(Nc) * Ks);
 }
-// resident scratch: cluster exchange vectors (two parities) and their
-// totals over the cluster, the FP64
-// multipliers xi', zeta' of the CTA, and the constants of their steps
-// (pmax_m, 1 / (ln2 mask_m), Psi_k) in FP32
+// resident scratch: the CTA's residual vector (two parities, read by the
+// other CTAs of its cluster), the multipliers xi', zeta' of the CTA as FP32
+// pairs, and the constants of their steps (pmax_m, 1 / (ln2 mask_m pmax_m),
+// Psi_k)
 HCRAN_HD int res_xch_floats(const KDims &k) {
   return int(al4(k.Mmax + 2 * (k.KSmax > 0 ? k.KSmax : 1) + 2));
 }
 HCRAN_HD int res_scratch_floats(const KDims &k) {
   const int m4 = int(al4(k.Mmax)), s4 = int(al4(k.KSmax > 0 ? k.KSmax : 1));
-  return 3 * res_xch_floats(k) + 2 * m4 + 2 * s4 + 2 * m4 + s4;  // + pmax, xi step scale, Psi
+  return 2 * res_xch_floats(k) + 2 * m4 + 2 * s4 + 2 * m4 + s4;
 }
 // Dynamic shared memory: streaming multipliers zeta' (FP32), the resident
 // scratch, then one region that holds either the per-warp buffers of the
@@ -259,21 +259,41 @@ inline void kdims_merge(KDims &a, const KDims &b) {
   a.KSmax = a.KSmax > b.KSmax ? a.KSmax : b.KSmax;
   a.res_floats = a.res_floats > b.res_floats ? a.res_floats : b.res_floats;
 }
-// Cluster sizes, largest first; launch class kNumClasses - 1 is the streamed
-// schedule (one CTA, subcarrier state staged from global memory) for
-// instances whose resident state does not fit even the largest cluster.
-constexpr int kNumClasses = 5;
-HCRAN_HD int class_csize(int cls) { return cls < 4 ? 8 >> cls : 1; }
+// Launch classes: class k < kMaxCluster holds the instances solved by
+// clusters of kMaxCluster - k CTAs (largest first); class kNumClasses - 1 is
+// the streamed schedule (one CTA, subcarrier state staged from global memory)
+// for instances whose resident state fits no cluster.
+constexpr int kMaxCluster = 8;  // portable cluster size limit
+constexpr int kNumClasses = kMaxCluster + 1;
+HCRAN_HD int class_csize(int cls) { return cls < kMaxCluster ? kMaxCluster - cls : 1; }
+HCRAN_HD int class_of(int C) { return kMaxCluster - C; }
 // margin kept free for the per-launch maxima of the other instances of a class
 constexpr int kClassMargin = 4096;
-// launch class of one instance: the smallest cluster whose resident state fits
+// SM cycles of one resident dual iteration on a CTA that holds g (n, m)
+// groups, measured on GB300 over the uneven batch: about 7000 + 6 g while
+// every thread holds at most one group (the stages are bound by the latency
+// of a group's chain, not by the number of groups), and about 3400 more for
+// each further group per thread.
+inline double res_iter_cycles(int64_t g) {
+  const int64_t per = (g + kThreads - 1) / kThreads;
+  return 7000.0 + 6.0 * double(g < kThreads ? g : kThreads) + 3400.0 * double(per > 1 ? per - 1 : 0);
+}
+// launch class of one instance: among the cluster sizes whose resident state
+// fits, the one with the fewest SM cycles per dual iteration, C times the
+// cycles of a CTA holding ceil(N / C) M groups (ties: the smaller cluster);
+// the streamed class when none fits
 inline int pick_class(int M, int l, int Ks, int N) {
-  for (int cls = 3; cls >= 0; cls--) {
-    const int C = class_csize(cls);
-    if (C > N) break;
-    if (dyn_smem_bytes(resident_kdims(M, l, Ks, N, C)) <= kMaxDynSmem - kClassMargin) return cls;
+  int best = kNumClasses - 1;
+  double best_cost = 0.0;
+  for (int C = 1; C <= kMaxCluster && C <= N; C++) {
+    if (dyn_smem_bytes(resident_kdims(M, l, Ks, N, C)) > kMaxDynSmem - kClassMargin) continue;
+    const double cost = C * res_iter_cycles(int64_t((N + C - 1) / C) * M);
+    if (best == kNumClasses - 1 || cost < best_cost) {
+      best = class_of(C);
+      best_cost = cost;
+    }
   }
-  return kNumClasses - 1;
+  return best;
 }
 // candidate-utility chunks of an instance solved by clusters of C CTAs: a
 // multiple of C, so that every CTA sums chunks of its own subcarriers

@@ -196,12 +196,12 @@ class Solver:
             C.c_void_p(self.workspace.data_ptr()), C.c_void_p(self.stream.cuda_stream)))
 
     def set_schedule(self, cluster_size):
-        """Cluster size per instance (1, 2, 4, 8; 0: one CTA streaming from global memory)."""
+        """Cluster size per instance (1 .. 8; 0: one CTA streaming from global memory)."""
         a = np.ascontiguousarray(cluster_size, dtype=np.int32)
         _check("hcran_set_schedule", self.lib.hcran_set_schedule(self.h, a.ctypes.data_as(_ip)))
 
     def autotune(self, gains, tol: Tol, max_dual_probe: int = 60) -> np.ndarray:
-        """Time each cluster-size class against clusters twice as large; keep the faster. Returns the schedule."""
+        """Time each cluster-size class C < 8 against clusters of min(2 C, 8); keep the faster. Returns the schedule."""
         _check("hcran_autotune", self.lib.hcran_autotune(
             self.h, C.c_void_p(gains.data_ptr()), C.byref(tol), C.c_void_p(self.workspace.data_ptr()),
             C.c_void_p(self.stream.cuda_stream), int(max_dual_probe)))

@@ -129,7 +129,15 @@ def _res_bytes(M, l, Ks, Nc):
                 + al4(Nc * ((Mi + 31) // 32)) + 2 * al4(Nc * Ks))
 
 
-def test_schedule_picks_smallest_cluster_that_holds_the_state():
+def _iter_cycles(g):
+    """Per-iteration cost of a CTA holding g (n, m) groups, restated from the
+    planner's model: flat up to one group per thread (512), then about 3400
+    cycles per further group per thread."""
+    per = -(-g // 512)
+    return 7000 + 6 * min(g, 512) + 3400 * max(per - 1, 0)
+
+
+def test_schedule_picks_cheapest_cluster_that_holds_the_state():
     lib = hcran.load()
     insts = make_workload("batch-4096-uneven", count=64) + make_workload("large-33x1024x512", count=1)
     made = [_cfg(i) for i in insts]
@@ -140,16 +148,18 @@ def test_schedule_picks_smallest_cluster_that_holds_the_state():
     assert lib.hcran_get_schedule(h, cs.ctypes.data_as(hcran._ip)) == 0
     assert lib.hcran_get_schedule(h, None) == 1
     lib.hcran_destroy(h)
-    assert set(cs.tolist()) <= {0, 1, 2, 4, 8}
+    assert set(cs.tolist()) <= set(range(9))
     assert cs[-1] == 0  # 33 x 1024 x 512: streamed from global memory
+    assert len(set(cs[:-1].tolist()) - {1, 2, 4, 8}) > 0  # sizes between the powers of two are used
     budget = 216 * 1024
+    cost = lambda inst, c: c * _iter_cycles(-(-inst.N // c) * inst.M)
     for inst, c in zip(insts[:-1], cs[:-1]):
-        assert c > 0
+        assert 0 < c <= min(8, inst.N)
         need = _res_bytes(inst.M, inst.l, inst.Ks, -(-inst.N // c))
         assert need < budget, (inst.M, inst.N, c, need)
-        if c > 1:  # the next smaller cluster would not hold the state
-            smaller = _res_bytes(inst.M, inst.l, inst.Ks, -(-inst.N // (c // 2)))
-            assert smaller > budget - 8 * 1024, (inst.M, inst.N, c, smaller)
+        for c2 in range(1, min(8, inst.N) + 1):  # no cluster size that clearly fits is cheaper
+            if _res_bytes(inst.M, inst.l, inst.Ks, -(-inst.N // c2)) <= budget - 8 * 1024:
+                assert cost(inst, c) <= cost(inst, c2), (inst.M, inst.N, c, c2)
 
 
 def test_set_schedule_validates_and_applies():
@@ -162,7 +172,7 @@ def test_set_schedule_validates_and_applies():
     n = len(insts)
     get = lambda: (lambda a: (lib.hcran_get_schedule(h, a.ctypes.data_as(hcran._ip)), a)[1])(np.zeros(n, np.int32))
     base = get()
-    bad = [np.where(np.arange(n) == 0, 3, base),                                   # not a cluster size
+    bad = [np.where(np.arange(n) == 0, 9, base),                                   # not a cluster size
            np.where(np.arange(n) == n - 1, 1, base),                               # 33x1024 state fits no CTA
            np.array([8 if i.N >= 8 else 1 for i in insts[:-1]] + [0]) * 0 + 16]    # too large a cluster
     for b in bad:
