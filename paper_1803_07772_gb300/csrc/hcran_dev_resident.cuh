@@ -339,17 +339,12 @@ __device__ __forceinline__ float power_stage_l(const Ctx &c, const Shared &sh, c
 
 // power stage: KKT power of the l slots of (n, m) from the sums of the last
 // link / sums stages and the current multipliers; RRH total at the new point.
-// Returns the thread's max |p_new - p| / mask.
+// L = l (1 .. 4) or 0 for any l.  Returns the thread's max |p_new - p| / mask.
+template <int L>
 __device__ __forceinline__ float stage_power(const Ctx &c, const Shared &sh, const RGeom &gm, const float *szeta,
                                              const GIt &gi) {
   const RView r = res_view(c, gm);
-  switch (c.l) {
-    case 1: return power_stage_l<1>(c, sh, r, szeta, gi);
-    case 2: return power_stage_l<2>(c, sh, r, szeta, gi);
-    case 3: return power_stage_l<3>(c, sh, r, szeta, gi);
-    case 4: return power_stage_l<4>(c, sh, r, szeta, gi);
-    default: break;
-  }
+  if (L > 0) return power_stage_l<(L > 0 ? L : 1)>(c, sh, r, szeta, gi);
   const int M = c.M, l = c.l, Up = c.Up, G = r.Nc * M;
   PowerCtx q;
   q.Ke = c.Ke;
@@ -506,16 +501,15 @@ __device__ __forceinline__ void link_stage_l(const Ctx &c, const Shared &sh, con
 }
 
 // link stage at the point in r.p (Sec. II-A SINR with the SIC order), then the
-// SIC step of (n, m): generation zc -> zc ^ 1 with step delta
+// SIC step of (n, m): generation zc -> zc ^ 1 with step delta.  L = l (1 .. 4)
+// or 0 for any l.
+template <int L>
 __device__ __forceinline__ void stage_link(const Ctx &c, const Shared &sh, const RGeom &gm, const float *szeta,
                                            float delta, int zc, const GIt &gi) {
   const RView r = res_view(c, gm);
-  switch (c.l) {
-    case 1: link_stage_l<1>(c, sh, r, szeta, delta, zc, gi); return;
-    case 2: link_stage_l<2>(c, sh, r, szeta, delta, zc, gi); return;
-    case 3: link_stage_l<3>(c, sh, r, szeta, delta, zc, gi); return;
-    case 4: link_stage_l<4>(c, sh, r, szeta, delta, zc, gi); return;
-    default: break;
+  if (L > 0) {
+    link_stage_l<(L > 0 ? L : 1)>(c, sh, r, szeta, delta, zc, gi);
+    return;
   }
   const int M = c.M, l = c.l, Up = c.Up, Rs = r.Rs, np = c.npair, Ks = c.Ks, Ke = c.Ke, G = r.Nc * M;
   const float sigma = c.sigma;
@@ -652,9 +646,12 @@ __device__ __forceinline__ void res_partials(const Ctx &c, const RGeom &gm, floa
 // iteration the stop test on max |p^v - p^{v-1}| / mask, the residual sums at
 // p^v with the steps of xi' and zeta' they give (beside the price and SIC
 // sums), the KKT power p^{v+1} and the link stage at p^{v+1}.  Returns the
-// iterations run.
-__device__ int dual_loop_res(const Ctx &c, Shared &sh, float *dyn, const KDims &kd, float *szeta,
-                             const Tol &tol, long long *cyc, unsigned &phase, unsigned &pending) {
+// iterations run.  Instantiated per l (L = 1 .. 4, 0 for any other l): the
+// loop is bound by the latency of short stages, and the code of one
+// instantiation stays compact in the instruction caches.
+template <int L>
+__device__ __forceinline__ int dual_loop_res_l(const Ctx &c, Shared &sh, float *dyn, const KDims &kd, float *szeta,
+                                               const Tol &tol, long long *cyc, unsigned &phase, unsigned &pending) {
   const int Vmax = tol.max_dual > 0 ? tol.max_dual : 1;
   const int M = c.M, Ks = c.Ks, nq = M + 2 * Ks;
   const RGeom r = res_geom(c, kd);
@@ -686,7 +683,7 @@ __device__ int dual_loop_res(const Ctx &c, Shared &sh, float *dyn, const KDims &
   stage_totals(c, r, gi);
   __syncthreads();
   int zc = 0;  // generation of the committed SIC multipliers
-  stage_link(c, sh, r, szeta, 1.f, zc, gi);
+  stage_link<L>(c, sh, r, szeta, 1.f, zc, gi);
   __syncthreads();
   if (threadIdx.x == 0) cyc[1] += clock64() - t0;
   int v = 0;
@@ -755,11 +752,11 @@ __device__ int dual_loop_res(const Ctx &c, Shared &sh, float *dyn, const KDims &
     }
     const long long t2 = clock64();
     zc ^= 1;  // the multipliers of the last link stage become the committed ones
-    float dl = stage_power(c, sh, r, szeta, gi);
+    float dl = stage_power<L>(c, sh, r, szeta, gi);
     dl = warp_max(dl);
     if (lane == 0) sh.redf[warp] = dl;
     __syncthreads();
-    stage_link(c, sh, r, szeta, rsqrtf((float)v + 2.f), zc, gi);
+    stage_link<L>(c, sh, r, szeta, rsqrtf((float)v + 2.f), zc, gi);
     __syncthreads();
     v++;
     const long long t3 = clock64();
@@ -776,6 +773,17 @@ __device__ int dual_loop_res(const Ctx &c, Shared &sh, float *dyn, const KDims &
   // gamma, pi, X, totals and SIC sums at the final point for the later phases
   link_all<kLinkOnly>(c, sh, dyn, kd, szeta, 0.f, phase, pending);
   return v;
+}
+
+__device__ int dual_loop_res(const Ctx &c, Shared &sh, float *dyn, const KDims &kd, float *szeta, const Tol &tol,
+                             long long *cyc, unsigned &phase, unsigned &pending) {
+  switch (c.l) {
+    case 1: return dual_loop_res_l<1>(c, sh, dyn, kd, szeta, tol, cyc, phase, pending);
+    case 2: return dual_loop_res_l<2>(c, sh, dyn, kd, szeta, tol, cyc, phase, pending);
+    case 3: return dual_loop_res_l<3>(c, sh, dyn, kd, szeta, tol, cyc, phase, pending);
+    case 4: return dual_loop_res_l<4>(c, sh, dyn, kd, szeta, tol, cyc, phase, pending);
+    default: return dual_loop_res_l<0>(c, sh, dyn, kd, szeta, tol, cyc, phase, pending);
+  }
 }
 
 }  // namespace hcran
