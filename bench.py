@@ -198,12 +198,14 @@ def run_gpu(args):
 
     # schedule: the planner's cost-model choice, then the autotuner
     # (untimed); the timed steps replay one CUDA graph of the class launches
+    # (--no-graph: direct launches, the form a profiler can replay one by one)
     planned = solver.schedule()
     if not args.no_autotune:
         solver.autotune(g, tol, max_dual_probe=60)
     sched = solver.schedule()
+    step = solver.solve if args.no_graph else solver.solve_graph
     for _ in range(args.warmup):
-        solver.solve_graph(g, tol)
+        step(g, tol)
     stream.synchronize()
 
     if world > 1:
@@ -216,7 +218,7 @@ def run_gpu(args):
     ev0.record(stream)
     launches = 0
     for _ in range(args.steps):
-        solver.solve_graph(g, tol)
+        step(g, tol)
         launches += solver.launches()
     ev1.record(stream)
     stream.synchronize()
@@ -280,7 +282,8 @@ def run_gpu(args):
                        "schedule": {("streamed" if k == 0 else "cluster%d" % k): int(v)
                                     for k, v in zip(*np.unique(sched, return_counts=True))},
                        "schedule_changed_by_autotuner": int(np.sum(sched != planned)),
-                       "launch": "CUDA graph, one persistent launch per cluster size"},
+                       "launch": ("direct launches" if args.no_graph else "CUDA graph") +
+                                 ", one persistent launch per cluster size"},
             "gpu_launches": launches,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
@@ -436,6 +439,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the planner's schedule")
     ap.add_argument("--no-warm", action="store_true", help="skip the learned warm-start leg")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="launch the classes directly instead of replaying a CUDA graph (for profiler launch lists)")
     ap.add_argument("--profile-mlp", action="store_true",
                     help="one training step of the warm-start network on 2^20 rows (the case for ncu)")
     ap.add_argument("--warm-train", type=int, default=512, help="training instances of the warm start")
