@@ -4,7 +4,8 @@
 //   dense_kernel   out[t][p] = epi( sum_q A[t][q] * Bt[p][q] )   (M = 128 rows
 //                  per tile, N = P <= 256, K = Q in steps of 16): the forward
 //                  of a layer (A = activations, Bt = weights [out][in]) and
-//                  the gradient of its input (A = dZ, Bt = weights^T)
+//                  the gradient of its input (A = dZ, Bt = weights^T); loads,
+//                  MMA issue and epilogue run on separate warps, pipelined
 //   wgrad_kernel   partial[cta][p][q] = sum_t Dz[t][p] * H[t][q] over the
 //                  CTA's row tiles (the gradient of a weight matrix), then
 //   wgrad_reduce   dW = sum over CTAs in a fixed order
@@ -36,110 +37,219 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
   return *reinterpret_cast<const uint32_t *>(&h);
 }
 
-// 16-byte rows chunks of a [rows][Kt] BF16 matrix (global, row stride ld
-// elements) into the core-matrix layout at smem base; rows >= nrows are zero
-__device__ __forceinline__ void fill_core(unsigned char *base, const __nv_bfloat16 *g, int64_t row0, int64_t nrows,
-                                          int rows, int Kt, int64_t ld) {
-  const int per_row = Kt >> 3;
-  for (int i = threadIdx.x; i < rows * per_row; i += kTcThreads) {
-    const int r = i / per_row, j = i - r * per_row;
-    uint4 v = make_uint4(0u, 0u, 0u, 0u);
-    if (row0 + r < nrows) v = *reinterpret_cast<const uint4 *>(g + (row0 + r) * ld + 8 * j);
-    *reinterpret_cast<uint4 *>(base + tc::core_off(r, 8 * j, Kt)) = v;
+// The dense layer is a pipeline over the CTA's 128-row tiles, one role per
+// warp group (256 threads):
+//   warps 5-7  stream each tile of A in K-chunks of Kc columns (cp.async, 16
+//              bytes a thread, rows past T zero-filled) into a ring of
+//              kStages shared-memory slots in the core-matrix layout
+//   warp 4     (one thread) issues the tcgen05 MMAs of a chunk once its slot
+//              is full, commits the slot back to the producers, and commits
+//              the tile's accumulator to the epilogue
+//   warps 0-3  (one TMEM lane quadrant each) drain the accumulator through
+//              the epilogue into global memory
+// Two TMEM accumulators alternate between tiles, so a tile's epilogue runs
+// under the next tile's MMAs and loads; the weight matrix stays resident.
+// Every wait is bounded: a timeout sets the abort flag and *err, every role
+// leaves its loop, and the MMAs and copies in flight are drained before the
+// TMEM is freed.
+constexpr int kPipeThreads = 256;
+constexpr int kStages = 4;         // A-chunk ring slots
+constexpr int kProdThreads = 96;   // warps 5-7
+constexpr int kLag = 2;            // chunks a producer keeps in flight
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, uint32_t bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}" ::"r"(tc::saddr(bar)) : "memory");
+}
+// bounded wait that also gives up once another role has aborted
+__device__ __forceinline__ bool pipe_wait(uint64_t *bar, uint32_t parity, volatile int *abort) {
+  for (int i = 0; i < tc::kSpin; i++) {
+    if (tc::mbar_try(bar, parity)) return true;
+    if ((i & 255) == 255 && *abort) return false;
+  }
+  return false;
+}
+
+// epilogue of one tile: accumulator columns [0, P) of this thread's TMEM lane
+__device__ __forceinline__ void dense_epilogue(uint32_t tacc, int warp, int lane, int64_t row0, int64_t T, int P,
+                                               int epi, const float *bias, const __nv_bfloat16 *H, void *out) {
+  const int64_t row = row0 + 32 * warp + lane;
+  for (int c0 = 0; c0 < P; c0 += 16) {
+    float v[16];
+    tc::tmem_ld16(tacc + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0, v);
+    if (row >= T) continue;
+    if (epi == kEpiBiasRelu || epi == kEpiBiasF32) {
+#pragma unroll
+      for (int i = 0; i < 16; i++) v[i] += bias ? bias[c0 + i] : 0.f;
+    }
+    if (epi == kEpiBiasRelu) {
+#pragma unroll
+      for (int i = 0; i < 16; i++) v[i] = fmaxf(v[i], 0.f);
+    } else if (epi == kEpiReluMask) {
+      const uint4 *hp = reinterpret_cast<const uint4 *>(H + row * P + c0);
+      const uint4 h0 = hp[0], h1 = hp[1];
+      const __nv_bfloat16 *hb0 = reinterpret_cast<const __nv_bfloat16 *>(&h0);
+      const __nv_bfloat16 *hb1 = reinterpret_cast<const __nv_bfloat16 *>(&h1);
+#pragma unroll
+      for (int i = 0; i < 8; i++) {
+        if (!(__bfloat162float(hb0[i]) > 0.f)) v[i] = 0.f;
+        if (!(__bfloat162float(hb1[i]) > 0.f)) v[8 + i] = 0.f;
+      }
+    }
+    if (epi == kEpiBiasF32 || epi == kEpiF32) {
+      float4 *o = reinterpret_cast<float4 *>(static_cast<float *>(out) + row * P + c0);
+#pragma unroll
+      for (int i = 0; i < 4; i++) o[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+    } else {
+      uint4 *o = reinterpret_cast<uint4 *>(static_cast<__nv_bfloat16 *>(out) + row * P + c0);
+      o[0] = make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]), pack_bf16(v[6], v[7]));
+      o[1] = make_uint4(pack_bf16(v[8], v[9]), pack_bf16(v[10], v[11]), pack_bf16(v[12], v[13]),
+                        pack_bf16(v[14], v[15]));
+    }
   }
 }
 
-__global__ void __launch_bounds__(kTcThreads, 1)
+// K-chunk width: the largest of 64, 32, 16 that divides Q
+__host__ __device__ __forceinline__ int dense_kc(int Q) { return (Q % 64 == 0) ? 64 : ((Q % 32 == 0) ? 32 : 16); }
+// TMEM columns of one accumulator (a power of two >= 32)
+__host__ __device__ __forceinline__ uint32_t dense_cols(int P) {
+  return P <= 32 ? 32u : (P <= 64 ? 64u : (P <= 128 ? 128u : 256u));
+}
+
+__global__ void __launch_bounds__(kPipeThreads, 1)
     dense_kernel(const __nv_bfloat16 *__restrict__ A, const __nv_bfloat16 *__restrict__ Bt,
                  const float *__restrict__ bias, const __nv_bfloat16 *__restrict__ H, int64_t T, int Q, int P,
                  int epi, void *__restrict__ out, int *err) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  __shared__ uint64_t bar;
+  __shared__ uint64_t full[kStages], empty[kStages], accf[2], acce[2], done;
   __shared__ uint32_t tslot;
+  __shared__ volatile int abort_flag;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  unsigned char *sA = smem;                      // [128][Q] core layout
-  unsigned char *sB = smem + kTile * Q * 2;      // [P][Q] core layout
-  const uint32_t ncols = P <= 32 ? 32u : (P <= 64 ? 64u : (P <= 128 ? 128u : 256u));
-  if (warp == 0) tc::tmem_alloc(&tslot, ncols);
+  const int Kc = dense_kc(Q), nchunk = Q / Kc;
+  const uint32_t chunk_bytes = (uint32_t)(kTile * Kc * 2);
+  unsigned char *sB = smem;                               // [P][Q] core layout, resident
+  unsigned char *ring = smem + (size_t)P * Q * 2;         // kStages x [128][Kc] core layout
+  const uint32_t ncols = dense_cols(P);
+  if (warp == 0) tc::tmem_alloc(&tslot, 2 * ncols);
   if (threadIdx.x == 0) {
-    tc::mbar_init(&bar, 1);
+    for (int i = 0; i < kStages; i++) {
+      tc::mbar_init(&full[i], kProdThreads);
+      tc::mbar_init(&empty[i], 1);
+    }
+    for (int b = 0; b < 2; b++) {
+      tc::mbar_init(&accf[b], 1);
+      tc::mbar_init(&acce[b], 4);
+    }
+    tc::mbar_init(&done, 1);
+    abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  fill_core(sB, Bt, 0, P, P, Q, Q);
+  for (int i = threadIdx.x; i < P * (Q >> 3); i += kPipeThreads) {  // weights into the core layout
+    const int r = i / (Q >> 3), j = i - r * (Q >> 3);
+    *reinterpret_cast<uint4 *>(sB + tc::core_off(r, 8 * j, Q)) = *reinterpret_cast<const uint4 *>(Bt + (int64_t)r * Q + 8 * j);
+  }
+  tc::fence_async_smem();
   tc::tc_fence_before();
   __syncthreads();
   tc::tc_fence_after();
   const uint32_t taddr = tslot;
-  const uint32_t idesc = tc::idesc_bf16(kTile, P);
-  const uint32_t sbo = (uint32_t)(Q >> 3) << 7;
   const int64_t ntiles = (T + kTile - 1) / kTile;
-  uint32_t phase = 0;
-  bool failed = false;
-  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int64_t row0 = tile * kTile;
-    fill_core(sA, A, row0, T, kTile, Q, Q);
-    tc::fence_async_smem();
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      tc::tc_fence_after();
-      for (int s = 0; s < (Q >> 4); s++) {
-        const uint64_t ad = tc::sdesc(tc::saddr(sA) + 256u * s, 128u, sbo);
-        const uint64_t bd = tc::sdesc(tc::saddr(sB) + 256u * s, 128u, sbo);
-        tc::mma_bf16(taddr, ad, bd, idesc, s > 0 ? 1u : 0u);
-      }
-      tc::mma_commit(&bar);
-    }
-    const bool ok = tc::mbar_wait(&bar, phase);
-    phase ^= 1u;
-    if (__syncthreads_or(!ok)) {  // block-uniform: every thread leaves together
-      failed = true;
-      break;
-    }
-    tc::tc_fence_after();
-    const int r = 32 * warp + lane;
-    const int64_t row = row0 + r;
-    for (int c0 = 0; c0 < P; c0 += 16) {
-      float v[16];
-      tc::tmem_ld16(taddr + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0, v);
-      if (row >= T) continue;
-      if (epi == kEpiBiasRelu || epi == kEpiBiasF32) {
-#pragma unroll
-        for (int i = 0; i < 16; i++) v[i] += bias ? bias[c0 + i] : 0.f;
-      }
-      if (epi == kEpiBiasRelu) {
-#pragma unroll
-        for (int i = 0; i < 16; i++) v[i] = fmaxf(v[i], 0.f);
-      } else if (epi == kEpiReluMask) {
-        const uint4 *hp = reinterpret_cast<const uint4 *>(H + row * P + c0);
-        const uint4 h0 = hp[0], h1 = hp[1];
-        const __nv_bfloat16 *hb0 = reinterpret_cast<const __nv_bfloat16 *>(&h0);
-        const __nv_bfloat16 *hb1 = reinterpret_cast<const __nv_bfloat16 *>(&h1);
-#pragma unroll
-        for (int i = 0; i < 8; i++) {
-          if (!(__bfloat162float(hb0[i]) > 0.f)) v[i] = 0.f;
-          if (!(__bfloat162float(hb1[i]) > 0.f)) v[8 + i] = 0.f;
+  const int mine = ntiles > blockIdx.x ? (int)((ntiles - 1 - blockIdx.x) / gridDim.x) + 1 : 0;
+
+  if (warp >= 5) {  // producers
+    const int pt = threadIdx.x - 160;
+    const int per_row = Kc >> 3;
+    int g = 0;
+    for (int i = 0; i < mine && !abort_flag; i++) {
+      const int64_t row0 = (blockIdx.x + (int64_t)i * gridDim.x) * kTile;
+      for (int c = 0; c < nchunk; c++, g++) {
+        const int s = g % kStages, u = g / kStages;
+        if (u >= 1 && !pipe_wait(&empty[s], (uint32_t)((u - 1) & 1), &abort_flag)) {
+          abort_flag = 1;
+          break;
+        }
+        const uint32_t dst0 = tc::saddr(ring + (size_t)s * chunk_bytes);
+        for (int q = pt; q < kTile * per_row; q += kProdThreads) {
+          const int r = q / per_row, j = q - r * per_row;
+          const bool in = row0 + r < T;
+          const __nv_bfloat16 *src = A + (in ? (row0 + r) * Q : 0) + c * Kc + 8 * j;
+          cp_async16(dst0 + tc::core_off(r, 8 * j, Kc), src, in ? 16u : 0u);
+        }
+        cp_async_commit();
+        if (g >= kLag) {  // chunk g - kLag has landed: publish it to the tensor core
+          cp_async_wait<kLag>();
+          tc::fence_async_smem();
+          mbar_arrive(&full[(g - kLag) % kStages]);
         }
       }
-      if (epi == kEpiBiasF32 || epi == kEpiF32) {
-        float4 *o = reinterpret_cast<float4 *>(static_cast<float *>(out) + row * P + c0);
-#pragma unroll
-        for (int i = 0; i < 4; i++) o[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
-      } else {
-        uint4 *o = reinterpret_cast<uint4 *>(static_cast<__nv_bfloat16 *>(out) + row * P + c0);
-        o[0] = make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]), pack_bf16(v[6], v[7]));
-        o[1] = make_uint4(pack_bf16(v[8], v[9]), pack_bf16(v[10], v[11]), pack_bf16(v[12], v[13]),
-                          pack_bf16(v[14], v[15]));
-      }
     }
-    tc::tc_fence_before();
-    __syncthreads();  // TMEM and the A tile are free for the next tile
+    cp_async_wait<0>();
+    tc::fence_async_smem();
+    if (!abort_flag)
+      for (int k = g - kLag > 0 ? g - kLag : 0; k < g; k++) mbar_arrive(&full[k % kStages]);
+  } else if (warp == 4) {  // MMA issue
+    if (lane == 0) {
+      const uint32_t idesc = tc::idesc_bf16(kTile, P);
+      const uint32_t sbo_a = (uint32_t)(Kc >> 3) << 7, sbo_b = (uint32_t)(Q >> 3) << 7;
+      int g = 0;
+      for (int i = 0; i < mine && !abort_flag; i++) {
+        const int b = i & 1;
+        if (i >= 2 && !pipe_wait(&acce[b], (uint32_t)(((i >> 1) - 1) & 1), &abort_flag)) {
+          abort_flag = 1;
+          break;
+        }
+        tc::tc_fence_after();
+        const uint32_t tacc = taddr + (uint32_t)b * ncols;
+        for (int c = 0; c < nchunk; c++, g++) {
+          const int s = g % kStages, u = g / kStages;
+          if (!pipe_wait(&full[s], (uint32_t)(u & 1), &abort_flag)) {
+            abort_flag = 1;
+            break;
+          }
+          tc::tc_fence_after();
+          const uint32_t a0 = tc::saddr(ring + (size_t)s * chunk_bytes), b0 = tc::saddr(sB);
+          for (int k = 0; k < (Kc >> 4); k++) {
+            const uint64_t ad = tc::sdesc(a0 + 256u * k, 128u, sbo_a);
+            const uint64_t bd = tc::sdesc(b0 + 256u * (c * (Kc >> 4) + k), 128u, sbo_b);
+            tc::mma_bf16(tacc, ad, bd, idesc, (c | k) ? 1u : 0u);
+          }
+          tc::mma_commit(&empty[s]);  // the slot is free once these MMAs complete
+        }
+        if (abort_flag) break;
+        tc::mma_commit(&accf[b]);
+      }
+      tc::mma_commit(&done);  // every MMA issued has completed when this arrives
+      if (!tc::mbar_wait(&done, 0u)) abort_flag = 1;
+    }
+    __syncwarp();
+  } else {  // epilogue (every exit warp-uniform: tcgen05.ld is warp-collective)
+    for (int i = 0; i < mine; i++) {
+      if (__any_sync(0xffffffffu, abort_flag != 0)) break;
+      const int b = i & 1;
+      const int64_t row0 = (blockIdx.x + (int64_t)i * gridDim.x) * kTile;
+      const bool ok = pipe_wait(&accf[b], (uint32_t)((i >> 1) & 1), &abort_flag);
+      if (__any_sync(0xffffffffu, !ok)) {  // warp-uniform exit
+        abort_flag = 1;
+        break;
+      }
+      tc::tc_fence_after();
+      dense_epilogue(taddr + (uint32_t)b * ncols, warp, lane, row0, T, P, epi, bias, H, out);
+      tc::tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acce[b]);
+    }
   }
-  if (failed) {
-    if (threadIdx.x == 0) atomicExch(err, 1);
-    tc::mbar_wait(&bar, phase ^ 1u);  // let an MMA still in flight finish (bounded)
-    __syncthreads();
-  }
-  if (warp == 0) tc::tmem_dealloc(taddr, ncols);
+  __syncthreads();
+  if (abort_flag && threadIdx.x == 0) atomicExch(err, 1);
+  tc::tc_fence_after();
+  if (warp == 0) tc::tmem_dealloc(taddr, 2 * ncols);
 }
 
 }  // namespace hcran
@@ -164,16 +274,17 @@ cudaError_t launch_dense(const void *A, const void *Bt, const float *bias, const
   int *err = nullptr;
   cudaError_t e = cudaGetSymbolAddress(reinterpret_cast<void **>(&err), g_tc_error);
   if (e != cudaSuccess) return e;
-  // at least 120 KB: one CTA per SM, so a TMEM allocation never waits on another CTA
-  const int need = kTile * Q * 2 + P * Q * 2;
+  // at least 120 KB: one CTA per SM, so the TMEM allocation (up to all 512
+  // columns) never waits on another CTA
+  const int need = P * Q * 2 + kStages * kTile * dense_kc(Q) * 2;
   const int smem = need > kOneCtaSmem ? need : kOneCtaSmem;
   e = cudaFuncSetAttribute(dense_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   const int64_t ntiles = (T + kTile - 1) / kTile;
   const int grid = (int)(ntiles < sm_count() ? ntiles : sm_count());
-  dense_kernel<<<grid, kTcThreads, smem, st>>>(static_cast<const __nv_bfloat16 *>(A),
-                                              static_cast<const __nv_bfloat16 *>(Bt), bias,
-                                              static_cast<const __nv_bfloat16 *>(H), T, Q, P, epi, out, err);
+  dense_kernel<<<grid, kPipeThreads, smem, st>>>(static_cast<const __nv_bfloat16 *>(A),
+                                                static_cast<const __nv_bfloat16 *>(Bt), bias,
+                                                static_cast<const __nv_bfloat16 *>(H), T, Q, P, epi, out, err);
   return cudaGetLastError();
 }
 }  // namespace hcran
