@@ -328,7 +328,7 @@ def warm_leg(args, solver, g, insts, tol, cold_summ, cold_ms, stream, dev):
         tgd = torch.from_numpy(tg).to(dev)
     X, Y, Mk = build_dataset(ts, tgd, tr, tol)
     del ts, tgd
-    net = MLP(seed=7, max_rows=1 << 15)
+    net = MLP(seed=7, max_rows=1 << 22)  # inference in chunks of 4M rows; training batches of 2^15
     hist = train(net, X, Y, Mk, epochs=args.warm_epochs, batch=1 << 15, lr=2e-3)
     train_s = time.time() - t0
     rows = solver.warm_rows()
