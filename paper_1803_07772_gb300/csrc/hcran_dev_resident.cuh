@@ -649,10 +649,11 @@ __device__ __forceinline__ void res_partials(const Ctx &c, const RGeom &gm, floa
 // iteration the stop test on max |p^v - p^{v-1}| / mask, the residual sums at
 // p^v with the steps of xi' and zeta' they give (beside the price and SIC
 // sums), the KKT power p^{v+1} and the link stage at p^{v+1}.  Returns the
-// iterations run.  Instantiated per l (L = 1 .. 4, 0 for any other l): the
-// loop is bound by the latency of short stages, and the code of one
-// instantiation stays compact in the instruction caches.
-template <int L>
+// iterations run.  Instantiated per l (L = 1 .. 4, 0 for any other l) and per
+// CL (a cluster of more than one CTA or not): the loop is bound by the latency
+// of short stages, and the code of one instantiation stays compact in the
+// instruction caches.
+template <int L, bool CL>
 __device__ __forceinline__ int dual_loop_res_l(const Ctx &c, Shared &sh, float *dyn, const KDims &kd, float *szeta,
                                                const Tol &tol, long long *cyc, unsigned &phase, unsigned &pending) {
   const int Vmax = tol.max_dual > 0 ? tol.max_dual : 1;
@@ -696,7 +697,7 @@ __device__ __forceinline__ int dual_loop_res_l(const Ctx &c, Shared &sh, float *
     // last power stage (0 before the first)
     const float dloc = warp_max(lane < kWarps ? sh.redf[lane] : 0.f);
     const float delta = rsqrtf((float)v + 1.f);
-    if (c.csize == 1) {
+    if (!CL) {
       if ((v > 0 && dloc < (float)tol.tol_dual) || v >= Vmax) break;
       if (u >= 0) {  // residual sums, then the multiplier steps they give
         res_partials(c, r, x.xch0);
@@ -780,12 +781,21 @@ __device__ __forceinline__ int dual_loop_res_l(const Ctx &c, Shared &sh, float *
 
 __device__ int dual_loop_res(const Ctx &c, Shared &sh, float *dyn, const KDims &kd, float *szeta, const Tol &tol,
                              long long *cyc, unsigned &phase, unsigned &pending) {
+  if (c.csize > 1) {
+    switch (c.l) {
+      case 1: return dual_loop_res_l<1, true>(c, sh, dyn, kd, szeta, tol, cyc, phase, pending);
+      case 2: return dual_loop_res_l<2, true>(c, sh, dyn, kd, szeta, tol, cyc, phase, pending);
+      case 3: return dual_loop_res_l<3, true>(c, sh, dyn, kd, szeta, tol, cyc, phase, pending);
+      case 4: return dual_loop_res_l<4, true>(c, sh, dyn, kd, szeta, tol, cyc, phase, pending);
+      default: return dual_loop_res_l<0, true>(c, sh, dyn, kd, szeta, tol, cyc, phase, pending);
+    }
+  }
   switch (c.l) {
-    case 1: return dual_loop_res_l<1>(c, sh, dyn, kd, szeta, tol, cyc, phase, pending);
-    case 2: return dual_loop_res_l<2>(c, sh, dyn, kd, szeta, tol, cyc, phase, pending);
-    case 3: return dual_loop_res_l<3>(c, sh, dyn, kd, szeta, tol, cyc, phase, pending);
-    case 4: return dual_loop_res_l<4>(c, sh, dyn, kd, szeta, tol, cyc, phase, pending);
-    default: return dual_loop_res_l<0>(c, sh, dyn, kd, szeta, tol, cyc, phase, pending);
+    case 1: return dual_loop_res_l<1, false>(c, sh, dyn, kd, szeta, tol, cyc, phase, pending);
+    case 2: return dual_loop_res_l<2, false>(c, sh, dyn, kd, szeta, tol, cyc, phase, pending);
+    case 3: return dual_loop_res_l<3, false>(c, sh, dyn, kd, szeta, tol, cyc, phase, pending);
+    case 4: return dual_loop_res_l<4, false>(c, sh, dyn, kd, szeta, tol, cyc, phase, pending);
+    default: return dual_loop_res_l<0, false>(c, sh, dyn, kd, szeta, tol, cyc, phase, pending);
   }
 }
 
