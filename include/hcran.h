@@ -24,8 +24,9 @@
  *  - Calls that take a stream only enqueue work on it; hcran_get* synchronise
  *    that stream before copying results to the caller's host arrays.
  *  - Arithmetic: SINR, power, prices and subgradient residuals in FP32;
- *    Dinkelbach ratio q = R/P, the F(q) test and the multiplier values
- *    (accumulated subgradient steps) in FP64.
+ *    the multipliers accumulate their subgradient steps as unevaluated
+ *    float pairs (about 48 significant bits) and are stored in FP64;
+ *    Dinkelbach ratio q = R/P and the F(q) test in FP64.
  */
 #ifndef HCRAN_H
 #define HCRAN_H

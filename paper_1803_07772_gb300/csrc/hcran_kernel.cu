@@ -1,8 +1,10 @@
 // hcran_kernel.cu -- persistent batched solver for sm_103a.
 //
-// One CTA (512 threads, 16 warps) solves one instance at a time and pulls the
-// next one from an LPT-ordered queue (largest M*N*K*l first).  The whole
-// method runs inside the CTA, so no CTA ever waits on another:
+// A thread-block cluster of C CTAs (C = 1 .. 8, 512 threads and 16 warps each)
+// solves one instance at a time and pulls the next one from the LPT-ordered
+// queue of its launch (largest M*N*K*l first).  CTA r of the cluster owns a
+// contiguous range of subcarriers; the CTAs exchange their per-iteration sums
+// through distributed shared memory, and no cluster ever waits on another:
 //
 //   p^0 (gain-based RRH choice, l strongest users, p = mask/l); E^1 = R/P
 //   Dinkelbach i (Sec. III):  selection  ->  Algorithm 1  ->  E^{i+1} = R/P
@@ -11,9 +13,10 @@
 //       xi', zeta', zeta_sic' -> closed-form KKT power of eq. (653)/(683)],
 //       then alpha/beta at the new point (eq. scale_approximation)
 //
-// Precision: FP32 for SINR, prices, powers and residuals; FP64 for q = R/P,
-// the F(q) test, the R and P sums and the multiplier values that accumulate
-// the subgradient steps.  Reductions run in a fixed order, so results are
+// Precision: FP32 for SINR, prices, powers and residuals; inside a dual loop
+// the multipliers accumulate their subgradient steps as (hi, lo) float pairs,
+// and between dual loops they are kept in FP64; FP64 for q = R/P, the F(q)
+// test and the R and P sums.  Reductions run in a fixed order, so results are
 // bit-reproducible run to run.  The pieces live in hcran_dev_*.cuh.
 #include "hcran_dev_warm.cuh"
 
