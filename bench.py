@@ -420,12 +420,46 @@ def run_profile_mlp():
     print(json.dumps({"profile_mlp_rows": T, "loss": float(loss.item()), "tc_failed": net.tc_failed()}))
 
 
+def _code_only(src: bytes) -> bytes:
+    """C/C++ source with comments removed and whitespace runs collapsed, so
+    that a comment edit does not count as a change of the device code."""
+    out, i, n, quote = [], 0, len(src), None
+    while i < n:
+        c = src[i:i + 1]
+        if quote:
+            out.append(c)
+            if c == b"\\":
+                out.append(src[i + 1:i + 2])
+                i += 2
+                continue
+            if c == quote:
+                quote = None
+        elif c in (b'"', b"'"):
+            quote = c
+            out.append(c)
+        elif src[i:i + 2] == b"//":
+            j = src.find(b"\n", i)
+            i = n if j < 0 else j
+            continue
+        elif src[i:i + 2] == b"/*":
+            j = src.find(b"*/", i + 2)
+            i = n if j < 0 else j + 2
+            out.append(b" ")
+            continue
+        else:
+            out.append(c)
+        i += 1
+    return b" ".join(b"".join(out).split())
+
+
 def kernel_hash(read=None) -> str:
+    """sha256 (first 16 hex digits) of the solve kernel's device source, comments
+    and whitespace removed."""
     import hashlib
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_1803_07772_gb300", "csrc")
     for f in KERNEL_FILES:
-        h.update(read(f) if read else open(os.path.join(d, f), "rb").read())
+        h.update(_code_only(read(f) if read else open(os.path.join(d, f), "rb").read()))
     return h.hexdigest()[:16]
 
 
