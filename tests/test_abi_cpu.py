@@ -187,3 +187,21 @@ def test_set_schedule_validates_and_applies():
     assert lib.hcran_set_schedule(h, everything_streamed.ctypes.data_as(hcran._ip)) == 0
     assert np.array_equal(get(), everything_streamed)
     lib.hcran_destroy(h)
+
+
+def test_kernel_hash_ignores_comments_but_not_code():
+    """The hash that ties the stored DRAM-traffic ratio to the device code:
+    comment and whitespace edits keep it, a code edit changes it."""
+    import bench
+    files = {f: open(os.path.join(os.path.dirname(hcran.__file__), "csrc", f), "rb").read()
+             for f in bench.KERNEL_FILES}
+    base = bench.kernel_hash(read=lambda f: files[f])
+    assert base == bench.kernel_hash()
+    commented = dict(files)
+    commented["hcran_layout.h"] = b"// a new comment\n/* and a block\n comment */\n" + files["hcran_layout.h"] + b"\n\n"
+    assert bench.kernel_hash(read=lambda f: commented[f]) == base
+    changed = dict(files)
+    changed["hcran_layout.h"] = files["hcran_layout.h"].replace(b"kClassMargin = 4096", b"kClassMargin = 4097")
+    assert changed["hcran_layout.h"] != files["hcran_layout.h"]
+    assert bench.kernel_hash(read=lambda f: changed[f]) != base
+    assert bench._code_only(b'x = "a//b"; // c\ny = \'/\'; /* d */ z;') == b'x = "a//b"; y = \'/\'; z;'
