@@ -722,23 +722,33 @@ __device__ __forceinline__ int dual_loop_res_l(const Ctx &c, Shared &sh, float *
       cluster_arrive();  // release: this thread's part of the vector is written
       stage_rows(c, sh, r, zc ^ 1, gi);
       cluster_wait();
-      // every load of a peer's vector is issued before the first is used
-      float dv[8];
+      // one round of peer loads: the maxima for the stop test and, on the
+      // threads that take a step, the values it sums, all issued before the
+      // first is used (totals in rank order)
+      const int i0 = threadIdx.x;
+      const bool upd = i0 < M + Ks, z0 = i0 >= M;
+      float dv[8], a[8], b[8];
 #pragma unroll
-      for (int q = 0; q < 8; q++) dv[q] = q < C ? peer(xv, q)[nq] : 0.f;
+      for (int q = 0; q < 8; q++) {
+        const float *pv = q < C ? peer(xv, q) : xv;
+        dv[q] = q < C ? pv[nq] : 0.f;
+        a[q] = q < C && upd ? pv[i0] : 0.f;
+        b[q] = q < C && upd && z0 ? pv[i0 + Ks] : 0.f;
+      }
       float d = dloc;
 #pragma unroll
       for (int q = 0; q < 8; q++) d = fmaxf(d, dv[q]);
       const bool stop = (v > 0 && d < (float)tol.tol_dual) || v >= Vmax;
-      if (!stop) {  // cluster totals in rank order, then the steps
-        for (int i = threadIdx.x; i < M + Ks; i += kThreads) {
+      if (!stop) {  // the steps
+        for (int i = i0; i < M + Ks; i += kThreads) {
           const bool z = i >= M;
-          float a[8], b[8];
+          if (i != i0) {  // only when M + Ks exceeds the block
 #pragma unroll
-          for (int q = 0; q < 8; q++) {
-            const float *pv = q < C ? peer(xv, q) : xv;
-            a[q] = q < C ? pv[i] : 0.f;
-            b[q] = q < C && z ? pv[i + Ks] : 0.f;
+            for (int q = 0; q < 8; q++) {
+              const float *pv = q < C ? peer(xv, q) : xv;
+              a[q] = q < C ? pv[i] : 0.f;
+              b[q] = q < C && z ? pv[i + Ks] : 0.f;
+            }
           }
           float t = a[0], t2 = b[0];
 #pragma unroll
