@@ -34,6 +34,31 @@ def rank_env():
             int(os.environ.get("LOCAL_RANK", "0")))
 
 
+# Under torchrun every rank solves its own batch (replicas, weak scaling): the
+# instances of rank r are the seeds [r * count, (r + 1) * count) of the
+# workload, the step time is the maximum over ranks, and the job value counts
+# every rank's instances.
+def rank_seed_start(rank: int, count: int) -> int:
+    return rank * count
+
+
+def max_over_ranks(x: float, device, world: int) -> float:
+    """Maximum of x over the ranks of the default process group (x itself
+    when there is one rank)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world: int, count: int, per_step_s: float) -> float:
+    """Instances per second of the whole job."""
+    return world * count / per_step_s
+
+
 # ---------------------------------------------------------------- CPU oracle leg
 
 def _oracle_one(args):
@@ -187,7 +212,7 @@ def run_gpu(args):
         cpu_line = cpu_baseline(os.cpu_count() or 1)
 
     count = args.instances
-    insts = make_workload(WORKLOAD, count=count, start=rank * count)
+    insts = make_workload(WORKLOAD, count=count, start=rank_seed_start(rank, count))
     gains, offs = pack_batch(insts)
     tol = make_tol(WORKLOADS[WORKLOAD]["tol"])
     stream = torch.cuda.Stream(dev)
@@ -225,11 +250,9 @@ def run_gpu(args):
     torch.cuda.synchronize(dev)
     ms = ev0.elapsed_time(ev1)
     clk = clocks.stop()
-    t = torch.tensor([ms], device=dev)
+    ms_max = max_over_ranks(ms, dev, world)
     if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
         dist.barrier()
-    ms_max = float(t.item())
     summ = solver.summary()
 
     # end to end through the C ABI from pinned host memory (copies inside the timed region)
@@ -239,11 +262,7 @@ def run_gpu(args):
     t0 = time.perf_counter()
     for _ in range(args.steps):
         ee_h, st_h = solver.solve_host(host, tol)
-    e2e_s = (time.perf_counter() - t0) / args.steps
-    te = torch.tensor([e2e_s], device=dev)
-    if world > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_s = float(te.item())
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / args.steps, dev, world)
 
     warm = None
     if not args.no_warm and world == 1:
@@ -251,7 +270,7 @@ def run_gpu(args):
 
     if rank == 0:
         per_step_ms = ms_max / args.steps
-        value = world * count / (per_step_ms / 1e3)
+        value = job_value(world, count, per_step_ms / 1e3)
         abytes = algorithmic_bytes(insts, summ["iters"])
         peaks = {}
         try:
@@ -289,7 +308,7 @@ def run_gpu(args):
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6.8 TB/s",
                          "algorithmic_bytes_per_launch": abytes},
-            "e2e": {"value": world * count / e2e_s, "unit": "instances/s",
+            "e2e": {"value": job_value(world, count, e2e_s), "unit": "instances/s",
                     "h2d_bytes_per_step": int(gains.nbytes),
                     "d2h_bytes_per_step": int(count * 8 + count * 4)},
             "solve_stats": {"mean_iters": np.mean(summ["iters"], axis=0).tolist(),
