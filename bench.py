@@ -267,6 +267,12 @@ def run_gpu(args):
     warm = None
     if not args.no_warm and world == 1:
         warm = warm_leg(args, solver, g, insts, tol, summ, ms_max / args.steps, stream, dev)
+    scen = None
+    if not args.no_scenarios and world == 1:
+        try:
+            scen = scenario_leg(dev)
+        except Exception as e:  # the main bench line stands on its own
+            scen = {"error": "%s: %s" % (type(e).__name__, e)}
 
     if rank == 0:
         per_step_ms = ms_max / args.steps
@@ -322,9 +328,45 @@ def run_gpu(args):
             out["cpu_baseline"] = cpu_line
         if warm:
             out["warm_start"] = warm
+        if scen:
+            out["scenarios"] = scen
         print(json.dumps(out), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def scenario_leg(dev):
+    """The architectures of Sec. VI (H-CRAN with NOMA and OMA, 1-tier C-RAN,
+    2-tier HCN, 1-tier HPN; 256 instances each, same seeds and users): solve
+    throughput and the mean elastic-user EE of each, timed with CUDA events
+    after 3 warm-up solves."""
+    import torch
+    from hcran_inputs import SCENARIOS, WORKLOADS, make_workload, pack_batch
+    from paper_1803_07772_gb300 import Solver, make_tol
+    out = {}
+    stream = torch.cuda.Stream(dev)
+    for name in SCENARIOS:
+        insts = make_workload(name)
+        gains, offs = pack_batch(insts)
+        with torch.cuda.stream(stream):
+            s = Solver(insts, gain_offsets=offs, device=str(dev), stream=stream)
+            g = torch.from_numpy(gains).to(dev)
+        tol = make_tol(WORKLOADS[name]["tol"])
+        for _ in range(3):
+            s.solve_graph(g, tol)
+        stream.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.solve_graph(g, tol)
+        e1.record(stream)
+        stream.synchronize()
+        summ = s.summary()
+        out[name] = {"instances_per_s": len(insts) / (e0.elapsed_time(e1) / 1e3),
+                     "mean_ee": float(np.mean(summ["ee"])),
+                     "streaming_unmet": int(np.sum((np.asarray(summ["status"]) & 2) != 0)),
+                     "mean_iters": np.mean(summ["iters"], axis=0).tolist()}
+        s.close()
+    return out
 
 
 MLP_FLOPS_PER_ROW = 2 * (16 * 256 + 256 * 256 + 256 * 256 + 256 * 16)  # forward, padded widths
@@ -492,6 +534,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the planner's schedule")
     ap.add_argument("--no-warm", action="store_true", help="skip the learned warm-start leg")
+    ap.add_argument("--no-scenarios", action="store_true", help="skip the Sec. VI architecture scenarios")
     ap.add_argument("--no-graph", action="store_true",
                     help="launch the classes directly instead of replaying a CUDA graph (for profiler launch lists)")
     ap.add_argument("--profile-mlp", action="store_true",

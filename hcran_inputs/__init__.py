@@ -6,6 +6,7 @@ holds none of the resource-allocation arithmetic, so both the FP64 oracle and
 the CUDA solver can be fed from it without sharing any solver code.
 """
 from .gen import (  # noqa: F401
+    SCENARIOS,
     Instance,
     Tolerances,
     WORKLOADS,

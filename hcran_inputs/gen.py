@@ -86,19 +86,38 @@ class Tolerances:
     max_dual: int = 200
 
 
-def _gains(seed: int, M: int, N: int, K: int) -> np.ndarray:
+def _sites(M: int, layout: str):
+    """RRH / base-station positions (m): "hcran" puts RRH 0 at the origin and
+    the others on a 200 m ring; "ring" puts all M on the ring; "pair" puts two
+    sites at (-250 m, 0) and (250 m, 0)."""
+    bx = np.zeros(M)
+    by = np.zeros(M)
+    if layout == "hcran":
+        for j in range(1, M):
+            a = 2.0 * math.pi * (j - 1) / (M - 1)
+            bx[j] = 200.0 * math.cos(a)
+            by[j] = 200.0 * math.sin(a)
+    elif layout == "ring":
+        for j in range(M):
+            a = 2.0 * math.pi * j / M
+            bx[j] = 200.0 * math.cos(a)
+            by[j] = 200.0 * math.sin(a)
+    elif layout == "pair":
+        if M != 2:
+            raise ValueError("the pair layout has two sites")
+        bx[:] = [-250.0, 250.0]
+    else:
+        raise ValueError("unknown layout " + layout)
+    return bx, by
+
+
+def _gains(seed: int, M: int, N: int, K: int, layout: str = "hcran") -> np.ndarray:
     u_r = splitmix64_uniform(seed, _S_RADIUS, K)
     u_t = splitmix64_uniform(seed, _S_ANGLE, K)
     r = 500.0 * np.sqrt(u_r)
     th = 2.0 * math.pi * u_t
     ux, uy = r * np.cos(th), r * np.sin(th)
-    Mf = M - 1
-    bx = np.zeros(M)
-    by = np.zeros(M)
-    for j in range(1, M):
-        a = 2.0 * math.pi * (j - 1) / Mf
-        bx[j] = 200.0 * math.cos(a)
-        by[j] = 200.0 * math.sin(a)
+    bx, by = _sites(M, layout)
     d = np.hypot(ux[None, :] - bx[:, None], uy[None, :] - by[:, None])   # [M, K] m
     d_km = np.maximum(d, 10.0) / 1000.0
     pl_db = 128.1 + 37.6 * np.log10(d_km)
@@ -117,19 +136,29 @@ def make_instance(seed: int, M: int, N: int, K: int, Ks: int, l: int,
                   pf_hpn: float = 3.0, pf_lpn: float = 1.0,
                   Bn_hz: float = 180e3, N0_dbm_per_hz: float = -174.0,
                   T_s: float = 0.05, rate_bps: float = 64e3,
-                  zbar_bits: float = 1024.0) -> Instance:
+                  zbar_bits: float = 1024.0, layout: str = "hcran",
+                  per_rrh: Optional[dict] = None) -> Instance:
+    """per_rrh: optional [M] arrays "pmax", "eta", "Pc", "Pf" that replace the
+    HPN / LPN constants (RRH 0 is the HPN, the others LPNs)."""
     if not (M >= 1 and N >= 1 and K >= 1 and 0 <= Ks <= K and l >= 1):
         raise ValueError("bad instance sizes")
     pmax = np.array([pmax_hpn] + [pmax_lpn] * (M - 1), dtype=np.float64)
     eta = np.array([eta_hpn] + [eta_lpn] * (M - 1), dtype=np.float64)
     Pc = np.array([pc_hpn] + [pc_lpn] * (M - 1), dtype=np.float64)
     Pf = np.array([pf_hpn] + [pf_lpn] * (M - 1), dtype=np.float64)
+    if per_rrh:
+        pmax = np.asarray(per_rrh.get("pmax", pmax), dtype=np.float64)
+        eta = np.asarray(per_rrh.get("eta", eta), dtype=np.float64)
+        Pc = np.asarray(per_rrh.get("Pc", Pc), dtype=np.float64)
+        Pf = np.asarray(per_rrh.get("Pf", Pf), dtype=np.float64)
+        if not all(a.shape == (M,) for a in (pmax, eta, Pc, Pf)):
+            raise ValueError("per-RRH constants must have M entries")
     N0 = 10.0 ** (N0_dbm_per_hz / 10.0) * 1e-3
     lam = rate_bps / zbar_bits
     return Instance(M=M, N=N, K=K, Ks=Ks, l=l, pmax=pmax, eta=eta, Pc=Pc, Pf=Pf,
                     Bn_hz=Bn_hz, N0_w_per_hz=N0,
                     T_s=np.full(Ks, T_s), lambda_pps=np.full(Ks, lam),
-                    zbar_bits=zbar_bits, G=_gains(seed, M, N, K), seed=seed)
+                    zbar_bits=zbar_bits, G=_gains(seed, M, N, K, layout), seed=seed)
 
 
 def _batch_sizes(seed: int):
@@ -159,6 +188,42 @@ def _large(i: int) -> Instance:
     return make_instance(500000 + i, M=33, N=1024, K=512, Ks=128, l=4)
 
 
+# The architectures compared in Sec. VI, each on 32 subcarriers with 12 users
+# of whom 6 stream (125 packets/s of 1024 bits, delay target 0.2 s):
+#   H-CRAN (NOMA and OMA)  one HPN and two LPN RRHs
+#   1-tier C-RAN           three LPN RRHs
+#   2-tier HCN             one macro BS and two pico BSs (static circuit power
+#                          10 W and 6.8 W, amplifier factor 4 for each)
+#   1-tier HPN             two macro BSs
+# Base stations of the HCN and HPN scenarios have no fronthaul power; macro
+# and pico BSs transmit at most the HPN's and the LPN's power.
+_SCEN_TRAFFIC = dict(N=32, K=12, Ks=6, T_s=0.2, rate_bps=125 * 1024.0)
+
+
+def _scen_hcran(i: int, l: int = 3) -> Instance:
+    return make_instance(600000 + i, M=3, l=l, **_SCEN_TRAFFIC)
+
+
+def _scen_hcran_oma(i: int) -> Instance:
+    return _scen_hcran(i, l=1)
+
+
+def _scen_cran(i: int) -> Instance:
+    return make_instance(600000 + i, M=3, l=3, layout="ring",
+                         per_rrh=dict(pmax=[1.0] * 3, eta=[2.0] * 3, Pc=[1.0] * 3, Pf=[1.0] * 3), **_SCEN_TRAFFIC)
+
+
+def _scen_hcn(i: int) -> Instance:
+    return make_instance(600000 + i, M=3, l=3,
+                         per_rrh=dict(pmax=[40.0, 1.0, 1.0], eta=[4.0] * 3, Pc=[10.0, 6.8, 6.8], Pf=[0.0] * 3),
+                         **_SCEN_TRAFFIC)
+
+
+def _scen_hpn(i: int) -> Instance:
+    return make_instance(600000 + i, M=2, l=3, layout="pair",
+                         per_rrh=dict(pmax=[40.0] * 2, eta=[4.0] * 2, Pc=[10.0] * 2, Pf=[0.0] * 2), **_SCEN_TRAFFIC)
+
+
 WORKLOADS: Dict[str, dict] = {
     # 1 HPN + 2 LPNs, 8 subcarriers, 4 elastic + 2 streaming users, l = 2
     "small-3x8x6": dict(make=_small, count=1, tol=Tolerances()),
@@ -169,7 +234,15 @@ WORKLOADS: Dict[str, dict] = {
     "batch-4096-uneven": dict(make=_batch, count=4096, tol=Tolerances()),
     # 1 HPN + 32 LPNs, 1024 subcarriers, 384 elastic + 128 streaming, l = 4
     "large-33x1024x512": dict(make=_large, count=256, tol=Tolerances()),
+    # the architectures of Sec. VI (same seeds and users in each)
+    "scenario-hcran-noma": dict(make=_scen_hcran, count=256, tol=Tolerances()),
+    "scenario-hcran-oma": dict(make=_scen_hcran_oma, count=256, tol=Tolerances()),
+    "scenario-cran-1tier": dict(make=_scen_cran, count=256, tol=Tolerances()),
+    "scenario-hcn-2tier": dict(make=_scen_hcn, count=256, tol=Tolerances()),
+    "scenario-hpn-1tier": dict(make=_scen_hpn, count=256, tol=Tolerances()),
 }
+SCENARIOS = ["scenario-hcran-noma", "scenario-hcran-oma", "scenario-cran-1tier", "scenario-hcn-2tier",
+             "scenario-hpn-1tier"]
 
 
 def make_workload(name: str, count: Optional[int] = None,

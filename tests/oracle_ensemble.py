@@ -25,16 +25,17 @@ NOISE_REL = 2.0 ** -24
 
 
 def _one(args):
-    inst, tol, kw, seed = args
+    inst, tol, kw, seed, noise = args
     if seed == 0:
         return oracle.solve(inst, tol, **kw)
-    return oracle.solve(inst, tol, noise_rel=NOISE_REL, noise_seed=seed, **kw)
+    return oracle.solve(inst, tol, noise_rel=noise, noise_seed=seed, **kw)
 
 
-def ensemble(inst, tol, n=7, **kw):
-    """Plain oracle result, then n perturbed ones (seeds 1..n)."""
+def ensemble(inst, tol, n=7, noise_rel=NOISE_REL, **kw):
+    """Plain oracle result, then n perturbed ones (seeds 1..n) with relative
+    noise noise_rel on every new dual-iteration power."""
     oracle.build()  # compile once before the workers start
-    jobs = [(inst, tol, kw, s) for s in range(n + 1)]
+    jobs = [(inst, tol, kw, s, noise_rel) for s in range(n + 1)]
     procs = max(1, min(len(jobs), os.cpu_count() or 1))
     with mp.get_context("spawn").Pool(procs) as pool:  # spawn: the parent may hold a CUDA context
         return pool.map(_one, jobs, chunksize=1)
