@@ -205,3 +205,24 @@ def test_kernel_hash_ignores_comments_but_not_code():
     assert changed["hcran_layout.h"] != files["hcran_layout.h"]
     assert bench.kernel_hash(read=lambda f: changed[f]) != base
     assert bench._code_only(b'x = "a//b"; // c\ny = \'/\'; /* d */ z;') == b'x = "a//b"; y = \'/\'; z;'
+
+
+def test_set_schedule_accepts_every_cluster_size_that_fits():
+    """Every cluster size 1..8 is a valid schedule for an instance whose state
+    fits and that has a subcarrier for each CTA; the schedule reads back as set."""
+    lib = hcran.load()
+    insts = make_workload("scenario-hcran-noma", count=2) + make_workload("small-3x8x6", count=1)
+    made = [_cfg(i) for i in insts]
+    arr = (hcran.Config * len(made))(*[m[0] for m in made])
+    h = C.c_void_p()
+    assert lib.hcran_create(C.byref(h), arr, len(made), None) == 0
+    n = len(insts)
+    for c in range(1, 9):
+        want = np.array([c, c, min(c, 8)], np.int32)  # 32, 32 and 8 subcarriers: every size fits
+        assert lib.hcran_set_schedule(h, want.ctypes.data_as(hcran._ip)) == 0, c
+        got = np.zeros(n, np.int32)
+        assert lib.hcran_get_schedule(h, got.ctypes.data_as(hcran._ip)) == 0
+        assert np.array_equal(got, want), (c, got)
+    too_many = np.array([1, 1, 9], np.int32)  # more CTAs than the portable cluster limit
+    assert lib.hcran_set_schedule(h, too_many.ctypes.data_as(hcran._ip)) == 1
+    lib.hcran_destroy(h)
