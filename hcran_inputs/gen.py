@@ -4,7 +4,9 @@ Channel model (Section II-A of arXiv 1803.07772 defines Gamma = |h|^2 per
 (RRH, user, subcarrier); the numeric model below follows the workload
 definitions used by this project, which replace the paper's d^-3 law):
 
-* HPN (RRH 0) at the origin; the M-1 LPNs on a 200 m ring at angles 2*pi*j/(M-1).
+* HPN (RRH 0) at the origin; the M-1 LPNs on a 200 m ring at angles 2*pi*j/(M-1)
+  (the architectures of Sec. VI also place all M sites on the ring, or two
+  sites at (-250 m, 0) and (250 m, 0); see `_sites`).
 * Users uniform by area in a 500 m disk; link distance clamped to >= 10 m.
 * Path loss 128.1 + 37.6 log10(d_km) dB, 8 dB log-normal shadowing i.i.d. per
   (RRH, user) and constant over subcarriers, Rayleigh power fading Exp(1)
