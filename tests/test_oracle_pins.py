@@ -216,7 +216,8 @@ def test_kkt_with_streaming_user():
 
 # ---------------------------------------------------------------- exact R, P, EE
 
-@pytest.mark.parametrize("name", ["small-3x8x6"])
+@pytest.mark.parametrize("name", ["small-3x8x6", "scenario-hcran-oma", "scenario-cran-1tier", "scenario-hcn-2tier",
+                                  "scenario-hpn-1tier"])
 def test_reported_R_P_match_independent_model(name):
     inst = make_workload(name)[0]
     r = oracle.solve(inst, WORKLOADS[name]["tol"])
