@@ -49,7 +49,7 @@ typedef enum {
 /* per-instance result status bits */
 #define HCRAN_ST_NOT_CONVERGED 1   /* Dinkelbach cap reached before F(q) <= tol * R */
 #define HCRAN_ST_STREAMING_UNMET 2 /* some streaming user ends below Psi_k (relative slack < -1e-3) */
-#define HCRAN_ST_EE_DECREASED 4    /* the stop test fired with F(q) < 0 (last pass lowered the EE) */
+#define HCRAN_ST_EE_DECREASED 4    /* the output's EE is below an earlier Dinkelbach iterate's (kept for C13) */
 #define HCRAN_ST_NUMERIC 8         /* non-finite value met; the instance's outputs are not valid */
 #define HCRAN_ST_TIMEOUT 16        /* a bounded wait for a shared-memory copy gave up; outputs not valid */
 

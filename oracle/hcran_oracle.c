@@ -31,11 +31,18 @@
  *  - SINR/interference of Sec. II-A with a strict SIC order (gain descending,
  *    lower user index first on equal gains); user k hears the stronger users
  *    of its own (m,n) and every selected link of the other RRHs on n.
+ *  - Power model: Sec. II-A builds the consumed power from the amplifier
+ *    power eta_m sum_{k in K} p of every RRH (all users), while the formula of
+ *    P(A, rho, p) that follows sums only the elastic users.  P here counts the
+ *    transmit power of every user, as the three-part power model states; with
+ *    streaming power left out of P a streaming user whose rate target is met
+ *    would have neither an energy price nor a rate price, and its power would
+ *    be undetermined (0/0 in eq. (683)).  EE = R(elastic) / P.
  *  - KKT powers: the terms of eq. (653)/(683) are derived from the Lagrangian
  *    of problem (final_Problem_formulation_1) in the log-power variable: a
  *    transmitter pays c*alpha/(ln2 * I) * Gamma for every victim it interferes
- *    with, c = w for elastic users and zeta'_k * w for streaming users; only
- *    elastic links carry the E^i * eta_m term (P counts elastic power only).
+ *    with, c = w for elastic users and zeta'_k * w for streaming users; every
+ *    link carries the E^i * eta_m term of P.
  *  - The outer iteration (eq. outer_iterative_algorithm) labels E^0 -> p^0 as
  *    its initialisation: p^0 is the initial feasible point, E^1 = R(p^0)/P(p^0),
  *    and iteration i >= 1 solves O5 at E^i starting from p^{i-1}.
@@ -44,19 +51,30 @@
  *    water-filling utility for every (m,k,n), A_k = argmax_m sum_n utility,
  *    then per (m,n) the users of m admitted greedily by utility while the
  *    set stays SIC-feasible (Omega_bar <= 0) and has at most l members.
+ *    C9 needs every streaming user served: a streaming user left without a
+ *    link is then given one, in user order, on the subcarrier of its RRH
+ *    (A_k, or argmax_m sum_n Gamma when A_k = -1) with the largest gain that
+ *    has a free slot or an elastic user, whom it displaces (the admitted
+ *    elastic user of least utility).  New links start at the water-filling
+ *    power, at least the floor.
  *  - C14 is used in the divided form Omega_bar = (sigma+X_k)/Gamma_k -
  *    (sigma+X_k')/Gamma_k', linear in the other RRHs' per-subcarrier powers;
  *    positive coefficients enter the denominator, negative ones the numerator
  *    at the SCALE linearisation point (the DC step of eq. C13e_new).
- *  - Subgradient steps (the paper fixes none): power budget and SIC use
- *    delta_v = 1/sqrt(v+1) on scaled residuals; the rate multiplier moves in
- *    log scale, zeta' <- zeta' * 2^clip((Psi - r_hat)/sum alpha, -1, 1), since
- *    r_hat is linear in log2 zeta'.  p stays in [1e-9 mask, mask]; alpha is
- *    evaluated at gamma >= 1e-12; the norms of the stopping tests are
- *    max |delta p| / mask over the selected links.
- *  - The stop test F <= xi of Sec. III is taken relative (F <= tol * R); it also
- *    ends the loop when an inexact inner solve gives F < 0, and, as the paper
- *    states, the last iterate is the output.
+ *  - Subgradient steps (the paper fixes none), all with the diminishing step
+ *    delta_v = 1/sqrt(v+1) of the dual loop: power budget and SIC on scaled
+ *    residuals; the rate multiplier in log scale,
+ *    zeta' <- zeta' * 2^(delta_v clip((Psi - r_hat)/sum alpha, -1, 1)),
+ *    since r_hat is linear in log2 zeta'.  p stays in [1e-9 mask, mask];
+ *    alpha is evaluated at gamma >= 1e-12; the norms of the stopping tests
+ *    are max |delta p| / mask over the selected links.
+ *  - The stop test F <= xi of Sec. III is taken relative (F <= tol * R).
+ *    Lemma 1 gives max_p R - E^i P >= 0, attained at least by p^{i-1} itself,
+ *    so an inner solve that ends below its start point (F < 0) is inexact:
+ *    the Dinkelbach iterate then stays p^{i-1} and the loop ends, provided
+ *    p^{i-1} meets the streaming rates (C13 with exact rates, within 1e-3) or
+ *    misses them by no more than p^i does; otherwise p^i is kept and the loop
+ *    goes on.
  */
 #include "hcran_oracle.h"
 
@@ -151,6 +169,19 @@ static int state_alloc(const inst_t *I, state_t *st) {
   st->zsic = calloc(NP, sizeof(double));
   return st->A && st->S && st->p && st->alpha && st->beta && st->plin && st->xi &&
          st->zeta && st->zsic;
+}
+static void state_copy(const inst_t *I, state_t *dst, const state_t *src) {
+  size_t L = (size_t)I->N * I->M * I->l;
+  size_t NP = (size_t)I->N * I->M * (I->npair > 0 ? I->npair : 1);
+  memcpy(dst->A, src->A, sizeof(int32_t) * I->K);
+  memcpy(dst->S, src->S, sizeof(int32_t) * L);
+  memcpy(dst->p, src->p, sizeof(double) * L);
+  memcpy(dst->alpha, src->alpha, sizeof(double) * L);
+  memcpy(dst->beta, src->beta, sizeof(double) * L);
+  memcpy(dst->plin, src->plin, sizeof(double) * L);
+  memcpy(dst->xi, src->xi, sizeof(double) * I->M);
+  memcpy(dst->zeta, src->zeta, sizeof(double) * (I->Ks > 0 ? I->Ks : 1));
+  memcpy(dst->zsic, src->zsic, sizeof(double) * NP);
 }
 static void state_free(state_t *st) {
   free(st->A); free(st->S); free(st->p); free(st->alpha); free(st->beta);
@@ -259,7 +290,8 @@ static double victim_price(const inst_t *I, const state_t *st, const double *pi,
 /* exact objective pieces (problem eq7)                                 */
 /* ------------------------------------------------------------------ */
 
-/* R = sum over elastic links of w log2(1+gamma); P = P_const + sum_m eta_m sum elastic p */
+/* R = sum over elastic links of w log2(1+gamma); P = P_const + sum_m eta_m sum p
+ * over every selected link (the power model of Sec. II-A) */
 static void exact_R_P(const inst_t *I, const state_t *st, double *R, double *P, double *Ptot) {
   rrh_totals(I, st, Ptot);
   double r = 0.0, tx = 0.0;
@@ -268,11 +300,12 @@ static void exact_R_P(const inst_t *I, const state_t *st, double *R, double *P, 
       for (int s = 0; s < I->l; s++) {
         size_t e = slot(I, n, m, s);
         int k = st->S[e];
-        if (k < 0 || k >= I->Ke) continue;
+        if (k < 0) continue;
+        tx += I->eta[m] * st->p[e];
+        if (k >= I->Ke) continue;
         double ie = noise_plus_interference(I, st, Ptot, n, m, s);
         double g = st->p[e] * gain(I, n, m, k) / ie;
         r += I->w[(size_t)m * I->K + k] * log2(1.0 + g);
-        tx += I->eta[m] * st->p[e];
       }
   *R = r;
   *P = I->Pconst + tx;
@@ -291,18 +324,20 @@ static void sort_sic(const inst_t *I, int n, int m, int *ids, int cnt) {
   }
 }
 
-static void initial_state(const inst_t *I, state_t *st) {
-  /* A_k = argmax_m sum_n Gamma_{m,k}^{(n)} */
-  for (int k = 0; k < I->K; k++) {
-    int best = 0;
-    double bestv = -1.0;
-    for (int m = 0; m < I->M; m++) {
-      double t = 0.0;
-      for (int n = 0; n < I->N; n++) t += gain(I, n, m, k);
-      if (t > bestv) { bestv = t; best = m; }
-    }
-    st->A[k] = best;
+/* argmax_m sum_n Gamma_{m,k}^{(n)} (lowest m on equal sums) */
+static int strongest_rrh(const inst_t *I, int k) {
+  int best = 0;
+  double bestv = -1.0;
+  for (int m = 0; m < I->M; m++) {
+    double t = 0.0;
+    for (int n = 0; n < I->N; n++) t += gain(I, n, m, k);
+    if (t > bestv) { bestv = t; best = m; }
   }
+  return best;
+}
+
+static void initial_state(const inst_t *I, state_t *st) {
+  for (int k = 0; k < I->K; k++) st->A[k] = strongest_rrh(I, k);
   /* S_{m,n} = the l strongest users served by m; p = mask/l */
   int *ids = malloc(sizeof(int) * I->K);
   for (int n = 0; n < I->N; n++)
@@ -394,7 +429,7 @@ static int select_links(const inst_t *I, state_t *st, double q, scratch_t *w,
         double gk = gain(I, n, m, k);
         double Ic = I->sigma + X + gk * Y;
         double g = gk / Ic;
-        double den = (k < I->Ke ? q * I->eta[m] : 0.0) + st->xi[m] +
+        double den = q * I->eta[m] + st->xi[m] +
                      victim_price(I, st, w->pi, n, m, k, k) + w->SICp[(size_t)n * M + m];
         double c = weight_c(I, st, m, k);
         double ps = waterfill(c, den, g, I->mask[m]);
@@ -469,7 +504,57 @@ static int select_links(const inst_t *I, state_t *st, double q, scratch_t *w,
       for (int s2 = 0; s2 < l; s2++) Snew[slot(I, n, m, s2)] = s2 < nc ? chosen[s2] : -1;
     }
 
-  /* new state: kept links keep p, alpha, beta; new links start at p* */
+  /* C9 needs every streaming user served: one left without a link gets one, in
+   * user order, on the subcarrier of its RRH with the largest gain (lowest n
+   * on equal gains) that has a free slot or an admitted elastic user; a full
+   * (m,n) gives up its elastic user of least utility (higher id on equal
+   * utility) */
+  for (int k = I->Ke; k < K; k++) {
+    int served = 0;
+    for (size_t e = 0; e < L && !served; e++)
+      if (Snew[e] == k) served = 1;
+    if (served) continue;
+    const int m = Anew[k] >= 0 ? Anew[k] : strongest_rrh(I, k);
+    Anew[k] = m;
+    int nb = -1, sb = -1;
+    double gb = -1.0;
+    for (int n = 0; n < N; n++) {
+      double g = gain(I, n, m, k);
+      if (!(g > gb)) continue;
+      int cnt = 0, rs = -1;
+      for (int s = 0; s < l; s++) {
+        int v = Snew[slot(I, n, m, s)];
+        if (v < 0) continue;
+        cnt++;
+        if (v >= I->Ke) continue;
+        double uv = w->u[((size_t)n * M + m) * K + v];
+        int vr = rs >= 0 ? Snew[slot(I, n, m, rs)] : -1;
+        double ur = rs >= 0 ? w->u[((size_t)n * M + m) * K + vr] : 0.0;
+        if (rs < 0 || uv < ur || (uv == ur && v > vr)) rs = s;
+      }
+      if (cnt < l || rs >= 0) { gb = g; nb = n; sb = cnt < l ? -1 : rs; }
+    }
+    if (nb < 0) continue; /* every (m,n) is full of streaming users */
+    int ids[64], cnt = 0;
+    for (int s = 0; s < l; s++) {
+      int v = Snew[slot(I, nb, m, s)];
+      if (v >= 0 && s != sb) ids[cnt++] = v;
+    }
+    if (sb >= 0) { /* margin of the displaced user against the next elastic one */
+      double ur = w->u[((size_t)nb * M + m) * K + Snew[slot(I, nb, m, sb)]];
+      for (int c = 0; c < cnt; c++)
+        if (ids[c] < I->Ke) {
+          double uo = w->u[((size_t)nb * M + m) * K + ids[c]];
+          track(fabs(uo - ur) / fmax(fabs(uo), fabs(ur)), tie_eps, min_margin, n_ties);
+        }
+    }
+    ids[cnt++] = k;
+    sort_sic(I, nb, m, ids, cnt);
+    for (int s = 0; s < l; s++) Snew[slot(I, nb, m, s)] = s < cnt ? ids[s] : -1;
+  }
+
+  /* new state: kept links keep p, alpha, beta; new links start at p*, at
+   * least the floor */
   for (int n = 0; n < N; n++)
     for (int m = 0; m < M; m++) {
       int same_set = 1;
@@ -489,7 +574,7 @@ static int select_links(const inst_t *I, state_t *st, double q, scratch_t *w,
           np_[s] = st->p[e]; na[s] = st->alpha[e]; nb[s] = st->beta[e]; nl[s] = st->plin[e];
         } else {
           size_t t = ((size_t)n * M + m) * K + k;
-          np_[s] = w->pstar[t];
+          np_[s] = w->pstar[t] > I->pfloor[m] ? w->pstar[t] : I->pfloor[m];
           nl[s] = np_[s];
           na[s] = 1.0;
           nb[s] = 0.0;
@@ -546,7 +631,7 @@ static double dual_iteration(const inst_t *I, state_t *st, double q, int v, scra
     double x = (I->Psi[ks] - r) / (asum > ZETA_ASUM_MIN ? asum : ZETA_ASUM_MIN);
     if (x > 1.0) x = 1.0;
     if (x < -1.0) x = -1.0;
-    double z = st->zeta[ks] * exp2(x);
+    double z = st->zeta[ks] * exp2(delta * x);
     if (z > ZETA_MAX) z = ZETA_MAX;
     if (z < ZETA_MIN) z = ZETA_MIN;
     st->zeta[ks] = z;
@@ -575,7 +660,7 @@ static double dual_iteration(const inst_t *I, state_t *st, double q, int v, scra
         size_t e = slot(I, n, m, s);
         int k = st->S[e];
         if (k < 0) { pnew[e] = 0.0; continue; }
-        double den = (k < I->Ke ? q * I->eta[m] : 0.0) + st->xi[m] +
+        double den = q * I->eta[m] + st->xi[m] +
                      victim_price(I, st, w->pi, n, m, k, -1) + w->SICp[(size_t)n * M + m];
         double num = weight_c(I, st, m, k) * st->alpha[e] / LN2 + w->SICm[(size_t)n * M + m] * st->plin[e];
         double pv;
@@ -603,6 +688,27 @@ static void scale_update(const inst_t *I, state_t *st, scratch_t *w) {
     double z = w->gam[e] > GAMMA_FLOOR ? w->gam[e] : GAMMA_FLOOR;
     orc_scale_coeffs(z, &st->alpha[e], &st->beta[e]);
   }
+}
+
+/* min over streaming users of (r_k - Psi_k) / Psi_k with exact rates (C13); 0 without streaming users */
+static double rate_slack_min(const inst_t *I, const state_t *st, double *Ptot) {
+  rrh_totals(I, st, Ptot);
+  double rmin = 1e300;
+  for (int ks = 0; ks < I->Ks; ks++) {
+    int k = I->Ke + ks;
+    double r = 0.0;
+    for (int n = 0; n < I->N; n++)
+      for (int m = 0; m < I->M; m++)
+        for (int s = 0; s < I->l; s++) {
+          size_t e = slot(I, n, m, s);
+          if (st->S[e] != k) continue;
+          double ie = noise_plus_interference(I, st, Ptot, n, m, s);
+          r += I->w[(size_t)m * I->K + k] * log2(1.0 + st->p[e] * gain(I, n, m, k) / ie);
+        }
+    double sl = (r - I->Psi[ks]) / I->Psi[ks];
+    if (sl < rmin) rmin = sl;
+  }
+  return I->Ks > 0 ? rmin : 0.0;
 }
 
 /* exact C12: scale an RRH's powers down when its total exceeds pmax */
@@ -669,8 +775,8 @@ int orc_solve(const orc_problem *pr, const orc_params *par, orc_result *out) {
   w.noise_seed = par->noise_seed;
   w.noise_ctr = 0;
   double *pstart = malloc(sizeof(double) * L);
-  state_t st;
-  int ok = state_alloc(&I, &st) && w.Ptot && w.Ie && w.u && w.pstar &&
+  state_t st, prev;
+  int ok = state_alloc(&I, &st) && state_alloc(&I, &prev) && w.Ptot && w.Ie && w.u && w.pstar &&
            w.keys && w.Xc && w.ids && pstart && I.mask && I.pfloor && I.Psi && I.w;
   int rc = 0;
   if (!ok) { rc = 2; goto done; }
@@ -681,6 +787,7 @@ int orc_solve(const orc_problem *pr, const orc_params *par, orc_result *out) {
   exact_R_P(&I, &st, &R, &P, w.Ptot);
   double q = par->q_init > 0.0 ? par->q_init : R / P;
   if (out->q_trace) out->q_trace[0] = q;
+  double slack_prev = rate_slack_min(&I, &st, w.Ptot), ee_best = R / P;
   double min_margin = 1.0;
   int n_ties = 0, it_d = 0, it_s = 0, it_v = 0, ntr = 0;
   const int Imax = par->max_dinkelbach > 0 ? par->max_dinkelbach : 1;
@@ -689,6 +796,8 @@ int orc_solve(const orc_problem *pr, const orc_params *par, orc_result *out) {
   int status = ST_NOT_CONVERGED;
 
   for (int i = 0; i < Imax; i++) {
+    state_copy(&I, &prev, &st); /* p^{i-1}, kept if Algorithm 1 ends below it */
+    const double q_prev = q;
     int changed = select_links(&I, &st, q, &w, par->tie_eps, &min_margin, &n_ties);
     /* ---- Algorithm 1 at E^i = q ---- */
     for (size_t e = 0; e < L; e++) { st.alpha[e] = 1.0; st.beta[e] = 0.0; }
@@ -724,10 +833,27 @@ int orc_solve(const orc_problem *pr, const orc_params *par, orc_result *out) {
     if (out->q_trace) out->q_trace[i + 1] = qn;
     if (out->F_trace) out->F_trace[i] = F;
     it_d++;
+    const double slack = rate_slack_min(&I, &st, w.Ptot);
+    if (F < 0.0) {
+      /* the inner solve ended below p^{i-1}, which attains F = 0 (Lemma 1):
+       * keep p^{i-1} and stop, unless p^{i-1} misses the streaming rates
+       * that p^i meets better */
+      if (slack_prev >= -1e-3 || slack_prev >= slack) {
+        state_copy(&I, &st, &prev);
+        q = q_prev;
+        status = 0;
+        break;
+      }
+      q = qn;
+      slack_prev = slack;
+      continue;
+    }
     q = qn;
-    /* stop test of Sec. III (F <= xi, relative here); the last iterate is the output */
+    slack_prev = slack;
+    if (qn > ee_best) ee_best = qn;
+    /* stop test of Sec. III (F <= xi, relative here) */
     if (F <= par->tol_dinkelbach * R) {
-      status = F < 0.0 ? ST_EE_DECREASED : 0;
+      status = 0;
       break;
     }
   }
@@ -763,6 +889,7 @@ int orc_solve(const orc_problem *pr, const orc_params *par, orc_result *out) {
     }
     out->slack_rate_min = I.Ks > 0 ? rmin : 0.0;
     if (I.Ks > 0 && rmin < -1e-3) status |= ST_STREAMING_UNMET;
+    if (out->ee < ee_best * (1.0 - 1e-9)) status |= ST_EE_DECREASED;
     double smax = -1e300;
     int npairs = 0;
     for (int n = 0; n < I.N; n++)
@@ -794,6 +921,7 @@ int orc_solve(const orc_problem *pr, const orc_params *par, orc_result *out) {
 
 done:
   state_free(&st);
+  state_free(&prev);
   free(w.Ptot); free(w.SICp); free(w.SICm); free(w.Ie); free(w.gam); free(w.pi);
   free(w.u); free(w.pstar); free(w.keys); free(w.Xc); free(w.ids);
   free(pstart);

@@ -62,7 +62,9 @@ typedef struct {
   /* scalars written by the oracle */
   double ee, R, P;
   int32_t iters[3];            /* Dinkelbach, SCALE (total), dual (total) */
-  int32_t status;              /* bit 0 not converged, bit 1 streaming rate unmet, bit 2 last Dinkelbach pass lowered the EE */
+  int32_t status;              /* bit 0 not converged (Dinkelbach cap), bit 1 a streaming rate unmet
+                                  (exact rate more than 1e-3 below Psi), bit 2 the output's EE is below
+                                  an earlier iterate's (one kept for the streaming rates) */
   double slack_power_min;      /* min_m (pmax - sum p)/pmax */
   double slack_rate_min;       /* min_k (r_k - Psi_k)/Psi_k over streaming users (exact rate) */
   double slack_sic_max;        /* max over selected pairs of Omega_bar / mask (<= 0 is feasible) */

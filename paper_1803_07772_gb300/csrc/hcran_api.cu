@@ -211,7 +211,7 @@ extern "C" int hcran_create(hcran_t *out, const hcran_config *cfgs, int32_t n,
       InstDesc &d = h->descs[b];
       const DLayout dl = dlayout(c.M, c.N, c.K, c.Ks, c.l);
       const FLayout fl = flayout(c.M, c.N, c.K, c.l, nchunk_cap(c.N, c.K));
-      const ILayout il = ilayout(c.M, c.N, c.K, c.l);
+      const ILayout il = ilayout(c.M, c.N, c.K, c.Ks, c.l);
       d.d_off = doff; doff += al4(dl.total);
       d.f_off = foff; foff += al4(fl.total);
       d.i_off = ioff; ioff += al4(il.total);
@@ -427,7 +427,7 @@ extern "C" int hcran_get(hcran_t h, int32_t index, hcran_result *out) {
   const InstDesc &d = h->descs[index];
   const DLayout dl = dlayout(d.M, d.N, d.K, d.Ks, d.l);
   const FLayout fl = flayout(d.M, d.N, d.K, d.l, nchunk_cap(d.N, d.K));
-  const ILayout il = ilayout(d.M, d.N, d.K, d.l);
+  const ILayout il = ilayout(d.M, d.N, d.K, d.Ks, d.l);
   const char *db = ws + h->ws.darena + sizeof(double) * d.d_off;
   const char *fb = ws + h->ws.farena + sizeof(float) * d.f_off;
   const char *ib = ws + h->ws.iarena + sizeof(int32_t) * d.i_off;

@@ -36,6 +36,13 @@ struct Ctx {
   float *p, *plin, *pstart, *alpha, *beta, *pi, *gam, *X, *Aden, *Bnum, *Cnum, *slab, *SICp, *SICm,
       *Ptot, *cu, *cp, *cX, *ckey, *Upart, *wf, *gown, *ginv, *wslot;
   int *A, *Anew, *S, *uslot;
+  int *Snew;   // [N][Up] selection being built, in SIC order
+  int *Again;  // [K] argmax_m sum_n Gamma_{m,k}
+  int *srv;    // [csize][Ks] streaming user served on this CTA's subcarriers
+  // the previous Dinkelbach iterate (kept when Algorithm 1 ends below it)
+  int *A_prev, *S_prev;
+  float *p_prev, *alpha_prev, *beta_prev;
+  double *xi_prev, *zeta_prev, *zsic_prev;
   float sigma;
   double Pconst;
   const double *Tdel;  // [Ks] delay targets (warm-start features)

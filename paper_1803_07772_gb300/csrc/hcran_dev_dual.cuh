@@ -138,7 +138,7 @@ __device__ int dual_loop(const Ctx &c, Shared &sh, float *dyn, const KDims &kd, 
           r += w0.wr[i * wstride + ks];
           as += w0.wa[i * wstride + ks];
         }
-        const float x = fminf(fmaxf((sh_psi(c, ks) - r) / fmaxf(as, (float)kZetaAsumMin), -1.f), 1.f);
+        const float x = delta * fminf(fmaxf((sh_psi(c, ks) - r) / fmaxf(as, (float)kZetaAsumMin), -1.f), 1.f);
         const double z = fmin(fmax(c.zeta[ks] * (double)exp2f(x), kZetaMin), kZetaMax);
         c.zeta[ks] = z;
         szeta[ks] = (float)z;
@@ -174,15 +174,18 @@ __device__ void scale_update(const Ctx &c) {
   __syncthreads();
 }
 
-// exact R (elastic, weighted) and P of problem (eq7) from the last link pass
+// exact R (elastic, weighted) of problem (eq7) and P of the Sec. II-A power
+// model (eta_m times the transmit power of every selected link) from the last
+// link pass
 __device__ void exact_R_P(const Ctx &c, Shared &sh, double &R, double &P) {
   double r = 0.0, tx = 0.0;
   for (int e = c.n0 * c.Up + threadIdx.x; e < c.n1 * c.Up; e += kThreads) {
     const int k = c.S[e];
-    if (k < 0 || k >= c.Ke) continue;
+    if (k < 0) continue;
     const int m = (e % c.Up) / c.l;
-    r += (double)c.w[(size_t)m * c.K + k] * (double)(log1pf(c.gam[e]) / LN2F);
     tx += c.eta[m] * (double)c.p[e];
+    if (k >= c.Ke) continue;
+    r += (double)c.w[(size_t)m * c.K + k] * (double)(log1pf(c.gam[e]) / LN2F);
   }
   R = cl_sum(r, sh, c);
   P = c.Pconst + cl_sum(tx, sh, c);

@@ -183,7 +183,7 @@ __device__ float power_subcarrier(const Ctx &c, const Shared &sh, const WarpBuf 
     }
     const int m = sh.slot_m[u];
     const float p = v.p[u];
-    const float den = (k < c.Ke ? sh.qeta[m] : 0.f) + sh.xif[m] + v.A[u];
+    const float den = sh.qeta[m] + sh.xif[m] + v.A[u];
     const float cw = k < c.Ke ? 1.f : szeta[k - c.Ke];
     const float num = cw * v.B[u] + v.C[u];
     const float mk = sh.maskf[m];

@@ -227,7 +227,7 @@ __device__ __forceinline__ void stage_totals(const Ctx &c, const RGeom &gm, cons
 
 // Projected subgradient steps from the residual sums of the last point:
 //   xi'_m        += delta (sum_n P_{m,n} - pmax_m) / (ln2 mask_m pmax_m), then [.]+
-//   log2 zeta'_k += clip((Psi_k - r_k) / max(sum_n alpha, 0.05), -1, 1), clipped
+//   log2 zeta'_k += delta clip((Psi_k - r_k) / max(sum_n alpha, 0.05), -1, 1), clipped
 // (C12 and C13-hat; the zeta' step is multiplicative, a sum in log2 scale),
 // accumulated in (hi, lo) float pairs.  The new xi'_m goes to sh.xif, the
 // new zeta'_k to szeta.
@@ -245,8 +245,9 @@ __device__ __forceinline__ void xi_update(const RScratch &x, Shared &sh, int m, 
   }
   sh.xif[m] = hi;
 }
-__device__ __forceinline__ void zeta_update(const RScratch &x, float *szeta, int ks, float rr, float as) {
-  const float e = fminf(fmaxf((x.psi[ks] - rr) / fmaxf(as, (float)kZetaAsumMin), -1.f), 1.f);
+__device__ __forceinline__ void zeta_update(const RScratch &x, float *szeta, int ks, float rr, float as,
+                                            float delta) {
+  const float e = delta * fminf(fmaxf((x.psi[ks] - rr) / fmaxf(as, (float)kZetaAsumMin), -1.f), 1.f);
   float hi = x.lzh[ks], lo = x.lzl[ks];
   ff_add(hi, lo, e);
   if (hi < kLog2ZetaMin) {
@@ -261,7 +262,7 @@ __device__ __forceinline__ void zeta_update(const RScratch &x, float *szeta, int
   szeta[ks] = exp2f(hi) * (1.f + lo * LN2F);
 }
 
-// KKT power of one slot (eq. 653 / 683): den = [elastic] q eta_m + xi'_m +
+// KKT power of one slot (eq. 653 / 683): den = q eta_m + xi'_m +
 // prices paid towards other RRHs' users + weaker users of (m, n) + SIC+;
 // num = c w alpha / ln2 + SIC- p_lin with c = 1 (elastic) or zeta'_k;
 // p = clip(num / den, p_floor, mask)
@@ -271,7 +272,7 @@ struct PowerCtx {
 };
 __device__ __forceinline__ float kkt_power(const PowerCtx &q, const float *szeta, int k, float own, float wa,
                                            float pl) {
-  const float den = (k < q.Ke ? q.qe : 0.f) + q.xf + (q.PIO + own + q.SP);
+  const float den = q.qe + q.xf + (q.PIO + own + q.SP);
   const float cw = k < q.Ke ? 1.f : szeta[k - q.Ke];
   const float num = cw * (wa * kInvLn2) + q.SM * pl;
   const float pv = (den <= 0.f || num >= den * q.mk) ? q.mk : num * fast_rcp(den);
@@ -703,9 +704,9 @@ __device__ __forceinline__ int dual_loop_res_l(const Ctx &c, Shared &sh, float *
         res_partials(c, r, x.xch0);
         asm volatile("bar.sync 1, %0;" ::"r"(P * 32) : "memory");
         if (u < M) xi_update(x, sh, u, x.xch0[u], delta);
-        else if (u < M + Ks) zeta_update(x, szeta, u - M, x.xch0[u], x.xch0[u + Ks]);
+        else if (u < M + Ks) zeta_update(x, szeta, u - M, x.xch0[u], x.xch0[u + Ks], delta);
         for (int ks = u - M + P * 32; ks < Ks; ks += P * 32)
-          zeta_update(x, szeta, ks, x.xch0[M + ks], x.xch0[M + Ks + ks]);
+          zeta_update(x, szeta, ks, x.xch0[M + ks], x.xch0[M + Ks + ks], delta);
       }
       stage_rows(c, sh, r, zc ^ 1, gi);
       __syncthreads();
@@ -758,7 +759,7 @@ __device__ __forceinline__ int dual_loop_res_l(const Ctx &c, Shared &sh, float *
               t2 += b[q];
             }
           if (!z) xi_update(x, sh, i, t, delta);
-          else zeta_update(x, szeta, i - M, t, t2);
+          else zeta_update(x, szeta, i - M, t, t2, delta);
         }
       }
       __syncthreads();

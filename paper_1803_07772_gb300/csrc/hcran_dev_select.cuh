@@ -39,7 +39,7 @@ __device__ float cand_utility(const Ctx &c, const Shared &sh, const float *szeta
       }
     }
   const float g = gk / (c.sigma + X + gk * Y);
-  const float den = (k < c.Ke ? sh.qeta[m] : 0.f) + sh.xif[m] + Pi + c.SICp[n * c.M + m];
+  const float den = sh.qeta[m] + sh.xif[m] + Pi + c.SICp[n * c.M + m];
   const float cw = weight_c(c, szeta, m, k);
   const float mk = sh.maskf[m];
   float ps;
@@ -105,8 +105,30 @@ __device__ int next_candidate(const Ctx &c, int n, int m, float lu, int lk, floa
   return bk;
 }
 
-// greedy SIC-feasible admission on (n, m); rewrites the slots of (n, m) in place
-__device__ bool admit(const Ctx &c, int n, int m, float tie_eps, float &mm, int &nt) {
+// SIC order on (m, n): gain descending, lower id first (insertion sort of a
+// short list)
+__device__ __forceinline__ void sort_sic(const Ctx &c, int n, int m, int *ids, int cnt) {
+  float cg[kMaxL];
+  for (int i = 0; i < cnt; i++) cg[i] = gain(c, n, m, ids[i]);
+  for (int i = 1; i < cnt; i++) {
+    const int x = ids[i];
+    const float gx = cg[i];
+    int j = i - 1;
+    while (j >= 0 && stronger(gx, x, cg[j], ids[j])) {
+      ids[j + 1] = ids[j];
+      cg[j + 1] = cg[j];
+      j--;
+    }
+    ids[j + 1] = x;
+    cg[j + 1] = gx;
+  }
+}
+
+// greedy SIC-feasible admission on (n, m): the users of m in (utility desc,
+// id asc) order while their utility is positive, each kept when every pair
+// with the users kept before satisfies Omega_bar <= 0, at most l; written to
+// Snew in SIC order
+__device__ void admit(const Ctx &c, int n, int m, float tie_eps, float &mm, int &nt) {
   int chosen[kMaxL];
   int nc = 0;
   float lu = INFINITY, bu;
@@ -139,21 +161,122 @@ __device__ bool admit(const Ctx &c, int n, int m, float tie_eps, float &mm, int 
     const float ul = c.cu[(size_t)n * c.K + chosen[c.l - 1]];
     if (k2 >= 0 && bu2 > 0.f) track((ul - bu2) / ul, tie_eps, mm, nt);
   }
-  // SIC order: gain descending, lower id first
-  float cg[kMaxL];
-  for (int i = 0; i < nc; i++) cg[i] = gain(c, n, m, chosen[i]);
-  for (int i = 1; i < nc; i++) {
-    const int x = chosen[i];
-    const float gx = cg[i];
-    int j = i - 1;
-    while (j >= 0 && stronger(gx, x, cg[j], chosen[j])) {
-      chosen[j + 1] = chosen[j];
-      cg[j + 1] = cg[j];
-      j--;
-    }
-    chosen[j + 1] = x;
-    cg[j + 1] = gx;
+  sort_sic(c, n, m, chosen, nc);
+  const int base = n * c.Up + m * c.l;
+  for (int s = 0; s < c.l; s++) c.Snew[base + s] = s < nc ? chosen[s] : -1;
+}
+
+// C9 needs every streaming user served.  A streaming user that admission left
+// without a link gets one, in user order, on the subcarrier of its RRH (A_k,
+// or Again_k when A_k = -1) with the largest gain (lowest n on equal gains)
+// where Snew has a free slot or an elastic user; a full (m, n) gives up its
+// elastic user of least utility (higher id on equal utility).  Runs on the
+// whole cluster; a user costs a few cluster barriers, and there is usually
+// none.
+__device__ void fixup_streaming(const Ctx &c, Shared &sh, float tie_eps, float &mm, int &nt) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // served flags of this CTA's subcarriers (admission only places k on A_k)
+  for (int ks = warp; ks < c.Ks; ks += kWarps) {
+    const int k = c.Ke + ks, m = c.Anew[k];
+    int f = 0;
+    if (m >= 0)
+      for (int n = c.n0 + lane; n < c.n1 && !f; n += 32)
+        for (int s = 0; s < c.l; s++)
+          if (c.Snew[n * c.Up + m * c.l + s] == k) f = 1;
+    f = __any_sync(0xffffffffu, f);
+    if (lane == 0) c.srv[c.crank * c.Ks + ks] = f;
   }
+  inst_sync(c);
+  for (int ks = 0; ks < c.Ks; ks++) {
+    int f = 0;
+    for (int r = 0; r < c.csize; r++) f |= c.srv[r * c.Ks + ks];
+    if (f) continue;  // the same decision on every thread of the cluster
+    const int k = c.Ke + ks;
+    const int m = c.Anew[k] >= 0 ? c.Anew[k] : c.Again[k];
+    // this CTA's eligible subcarrier of largest gain (lowest n on ties)
+    if (warp == 0) {
+      float bg = -1.f;
+      int bn = -1;
+      for (int n = c.n0 + lane; n < c.n1; n += 32) {
+        int cnt = 0, el = 0;
+        for (int s = 0; s < c.l; s++) {
+          const int v = c.Snew[n * c.Up + m * c.l + s];
+          if (v < 0) continue;
+          cnt++;
+          if (v < c.Ke) el = 1;
+        }
+        if (cnt == c.l && !el) continue;
+        const float g = gain(c, n, m, k);
+        if (g > bg) {  // lanes visit n in increasing order: ties keep the lower n
+          bg = g;
+          bn = n;
+        }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const float og = __shfl_xor_sync(0xffffffffu, bg, o);
+        const int on = __shfl_xor_sync(0xffffffffu, bn, o);
+        if (on >= 0 && (bn < 0 || og > bg || (og == bg && on < bn))) {
+          bg = og;
+          bn = on;
+        }
+      }
+      if (lane == 0) {
+        sh.cxf = bg;
+        sh.cxi = bn;
+      }
+    }
+    inst_sync(c);
+    float bg = -1.f;
+    int bn = -1;
+    for (int r = 0; r < c.csize; r++) {  // CTA r holds higher subcarriers than r - 1
+      const float og = c.csize > 1 ? *peer(&sh.cxf, r) : sh.cxf;
+      const int on = c.csize > 1 ? *peer(&sh.cxi, r) : sh.cxi;
+      if (on >= 0 && (bn < 0 || og > bg)) {
+        bg = og;
+        bn = on;
+      }
+    }
+    if (bn >= c.n0 && bn < c.n1 && threadIdx.x == 0) {
+      const int base = bn * c.Up + m * c.l;
+      int ids[kMaxL], cnt = 0, rs = -1;
+      float ur = 0.f;
+      for (int s = 0; s < c.l; s++) {
+        const int v = c.Snew[base + s];
+        if (v < 0 || v >= c.Ke) continue;
+        const float uv = c.cu[(size_t)bn * c.K + v];
+        const int vr = rs >= 0 ? c.Snew[base + rs] : -1;
+        if (rs < 0 || uv < ur || (uv == ur && v > vr)) {
+          rs = s;
+          ur = uv;
+        }
+      }
+      int full = 0;
+      for (int s = 0; s < c.l; s++) full += c.Snew[base + s] >= 0;
+      const int drop = full < c.l ? -1 : rs;
+      for (int s = 0; s < c.l; s++) {
+        const int v = c.Snew[base + s];
+        if (v >= 0 && s != drop) ids[cnt++] = v;
+      }
+      if (drop >= 0)  // margin of the displaced user against the other elastic users
+        for (int i = 0; i < cnt; i++)
+          if (ids[i] < c.Ke) {
+            const float uo = c.cu[(size_t)bn * c.K + ids[i]];
+            track(fabsf(uo - ur) / fmaxf(fabsf(uo), fabsf(ur)), tie_eps, mm, nt);
+          }
+      ids[cnt++] = k;
+      sort_sic(c, bn, m, ids, cnt);
+      for (int s = 0; s < c.l; s++) c.Snew[base + s] = s < cnt ? ids[s] : -1;
+    }
+    if (c.crank == 0 && threadIdx.x == 0) c.Anew[k] = m;
+    inst_sync(c);
+  }
+}
+
+// the new selection of (n, m) from Snew: kept links keep their power, new
+// links start at the water-filling power (at least the floor), dropped links
+// go to 0; alpha = 1, beta = 0; SIC multipliers reset where the set changed.
+// Returns true when the set changed.
+__device__ bool apply_selection(const Ctx &c, const Shared &sh, int n, int m) {
   const int base = n * c.Up + m * c.l;
   int oldk[kMaxL];
   float oldp[kMaxL], oldl[kMaxL];
@@ -162,25 +285,24 @@ __device__ bool admit(const Ctx &c, int n, int m, float tie_eps, float &mm, int 
     oldk[s] = c.S[base + s];
     oldp[s] = c.p[base + s];
     oldl[s] = c.plin[base + s];
-    if (oldk[s] != (s < nc ? chosen[s] : -1)) same = false;
+    if (oldk[s] != c.Snew[base + s]) same = false;
   }
   for (int s = 0; s < c.l; s++) {
     const int e = base + s;
-    if (s >= nc) {
-      c.S[e] = -1;
+    const int k = c.Snew[e];
+    c.S[e] = k;
+    if (k < 0) {
       c.p[e] = 0.f;
       c.plin[e] = 0.f;
     } else {
-      const int k = chosen[s];
       int old = -1;
       for (int b = 0; b < c.l; b++)
         if (oldk[b] == k) old = b;
-      c.S[e] = k;
-      if (old >= 0) {  // kept links keep their power
+      if (old >= 0) {
         c.p[e] = oldp[old];
         c.plin[e] = oldl[old];
-      } else {  // new links start at the water-filling power
-        c.p[e] = c.cp[(size_t)n * c.K + k];
+      } else {
+        c.p[e] = fmaxf(c.cp[(size_t)n * c.K + k], sh.floorf[m]);
         c.plin[e] = c.p[e];
       }
     }
@@ -235,9 +357,11 @@ __device__ int selection(const Ctx &c, Shared &sh, float *dyn, const KDims &kd, 
   }
   inst_sync(c);
   // (C) the candidate of every (n, k) on its chosen RRH
+  // (users with A_k = -1 have no candidate, except streaming users, whose
+  // candidate on Again_k gives the start power if the fix-up places them)
   for (int t = c.n0 * c.K + threadIdx.x; t < c.n1 * c.K; t += kThreads) {
     const int n = t / c.K, k = t - n * c.K;
-    const int m = c.Anew[k];
+    const int m = c.Anew[k] >= 0 ? c.Anew[k] : (k >= c.Ke ? c.Again[k] : -1);
     if (m < 0) {
       c.cu[t] = 0.f;
       c.cp[t] = 0.f;
@@ -252,9 +376,14 @@ __device__ int selection(const Ctx &c, Shared &sh, float *dyn, const KDims &kd, 
     c.ckey[t] = key;
   }
   __syncthreads();
-  // (D) admission per (n, m)
+  // (D) admission per (n, m) into Snew
+  for (int nm = c.n0 * c.M + threadIdx.x; nm < c.n1 * c.M; nm += kThreads) admit(c, nm / c.M, nm % c.M, tie_eps, mm, nt);
+  __syncthreads();
+  // (E) every streaming user served (synchronises the cluster)
+  if (c.Ks > 0) fixup_streaming(c, sh, tie_eps, mm, nt);
+  // (F) the new state from Snew
   for (int nm = c.n0 * c.M + threadIdx.x; nm < c.n1 * c.M; nm += kThreads)
-    if (admit(c, nm / c.M, nm % c.M, tie_eps, mm, nt)) ch_local = 1;
+    if (apply_selection(c, sh, nm / c.M, nm % c.M)) ch_local = 1;
   inst_sync(c);  // every CTA has read A
   for (int k = cl_first(c); k < c.K; k += cl_stride(c)) c.A[k] = c.Anew[k];
   __syncthreads();
@@ -271,7 +400,7 @@ __device__ int selection(const Ctx &c, Shared &sh, float *dyn, const KDims &kd, 
   return anych > 0;
 }
 
-// p^0: A_k = argmax_m sum_n Gamma, the l strongest users of m on every
+// p^0: A_k = Again_k = argmax_m sum_n Gamma, the l strongest users of m on every
 // subcarrier (already in SIC order), p = mask / l; xi' = 0, zeta' = 1.
 __device__ void initial_state(const Ctx &c, float *szeta) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -282,18 +411,19 @@ __device__ void initial_state(const Ctx &c, float *szeta) {
     c.alpha[e] = 1.f;
     c.beta[e] = 0.f;
   }
-  for (int k = cl_first(c); k < c.K; k += cl_stride(c)) {
+  for (int k = cl_first(c); k < c.K; k += cl_stride(c)) {  // FP64 sums in subcarrier order
     int best = 0;
-    float bv = -1.f;
+    double bv = -1.0;
     for (int m = 0; m < c.M; m++) {
-      float t = 0.f;
-      for (int n = 0; n < c.N; n++) t += gain(c, n, m, k);
+      double t = 0.0;
+      for (int n = 0; n < c.N; n++) t += (double)gain(c, n, m, k);
       if (t > bv) {
         bv = t;
         best = m;
       }
     }
     c.A[k] = best;
+    c.Again[k] = best;
   }
   inst_sync(c);
   for (int nm = c.n0 * c.M + warp; nm < c.n1 * c.M; nm += kWarps) {

@@ -7,7 +7,10 @@
 // through distributed shared memory, and no cluster ever waits on another:
 //
 //   p^0 (gain-based RRH choice, l strongest users, p = mask/l); E^1 = R/P
-//   Dinkelbach i (Sec. III):  selection  ->  Algorithm 1  ->  E^{i+1} = R/P
+//   Dinkelbach i (Sec. III):  selection  ->  Algorithm 1  ->  E^{i+1} = R/P;
+//     when Algorithm 1 ends below p^{i-1} (F < 0; Lemma 1 has p^{i-1} attain
+//     F = 0), p^{i-1} is kept and the loop ends, unless p^{i-1} misses the
+//     streaming rates that p^i meets better
 //     Algorithm 1 (Sec. IV-A): alpha = 1, beta = 0; SCALE passes, each a
 //       dual loop of [interference/SINR/prices -> projected subgradient on
 //       xi', zeta', zeta_sic' -> closed-form KKT power of eq. (653)/(683)],
@@ -21,6 +24,66 @@
 #include "hcran_dev_warm.cuh"
 
 namespace hcran {
+
+// min over streaming users of (r_k - Psi_k) / Psi_k with exact rates (C13)
+// from the last link pass, over the cluster (INFINITY without streaming users)
+__device__ float rate_slack_min(const Ctx &c, Shared &sh) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float rmin = INFINITY;
+  for (int base = 0; base < c.Ks; base += kMaxM) {  // streaming users in groups of kMaxM
+    const int cnt = c.Ks - base < kMaxM ? c.Ks - base : kMaxM;
+    for (int i = warp; i < cnt; i += kWarps) {
+      const int k = c.Ke + base + i;
+      const int a = c.A[k];
+      float r = 0.f;
+      if (a >= 0) {
+        const float wk = c.wf[(size_t)a * c.K + k];
+        for (int n = c.n0 + lane; n < c.n1; n += 32) {
+          const int u = c.uslot[(size_t)k * c.N + n];
+          if (u >= 0) r += wk * log1pf(c.gam[n * c.Up + u]) / LN2F;
+        }
+      }
+      r = warp_sum(r);
+      if (lane == 0) sh.vpart[i] = r;
+    }
+    cl_vsum(sh, c, cnt);
+    for (int i = threadIdx.x; i < cnt; i += kThreads)
+      rmin = fminf(rmin, (float)((sh.vtot[i] - c.Psi[base + i]) / c.Psi[base + i]));
+  }
+  return block_min(rmin, sh);
+}
+
+// copy of the Dinkelbach iterate p^{i-1} (this CTA's subcarriers; A, xi',
+// zeta' shared out over the cluster), and its restoration with the slab
+__device__ void save_iterate(const Ctx &c) {
+  for (int e = c.n0 * c.Up + threadIdx.x; e < c.n1 * c.Up; e += kThreads) {
+    c.S_prev[e] = c.S[e];
+    c.p_prev[e] = c.p[e];
+    c.alpha_prev[e] = c.alpha[e];
+    c.beta_prev[e] = c.beta[e];
+  }
+  for (int t = c.n0 * c.NPp + threadIdx.x; t < c.n1 * c.NPp; t += kThreads) c.zsic_prev[t] = c.zsic[t];
+  for (int k = cl_first(c); k < c.K; k += cl_stride(c)) c.A_prev[k] = c.A[k];
+  for (int m = cl_first(c); m < c.M; m += cl_stride(c)) c.xi_prev[m] = c.xi[m];
+  for (int k = cl_first(c); k < c.Ks; k += cl_stride(c)) c.zeta_prev[k] = c.zeta[k];
+  inst_sync(c);
+}
+__device__ void restore_iterate(const Ctx &c, float *szeta) {
+  for (int e = c.n0 * c.Up + threadIdx.x; e < c.n1 * c.Up; e += kThreads) {
+    c.S[e] = c.S_prev[e];
+    c.p[e] = c.p_prev[e];
+    c.plin[e] = c.p_prev[e];
+    c.alpha[e] = c.alpha_prev[e];
+    c.beta[e] = c.beta_prev[e];
+  }
+  for (int t = c.n0 * c.NPp + threadIdx.x; t < c.n1 * c.NPp; t += kThreads) c.zsic[t] = c.zsic_prev[t];
+  for (int k = cl_first(c); k < c.K; k += cl_stride(c)) c.A[k] = c.A_prev[k];
+  for (int m = cl_first(c); m < c.M; m += cl_stride(c)) c.xi[m] = c.xi_prev[m];
+  for (int k = cl_first(c); k < c.Ks; k += cl_stride(c)) c.zeta[k] = c.zeta_prev[k];
+  inst_sync(c);
+  for (int k = threadIdx.x; k < c.Ks; k += kThreads) szeta[k] = (float)c.zeta[k];
+  build_slab(c);
+}
 
 __device__ void solve_instance(const Ctx &c, Shared &sh, float *dyn, const KDims &kd, const Tol &tol,
                                InstOut *out, unsigned &phase, unsigned &pending) {
@@ -76,7 +139,11 @@ __device__ void solve_instance(const Ctx &c, Shared &sh, float *dyn, const KDims
   int it_d = 0, it_s = 0, it_v = 0, status = 1;  // not converged until the stop test fires
   const int Imax = tol.max_dinkelbach > 0 ? tol.max_dinkelbach : 1;
   const int Smax = tol.max_scale > 0 ? tol.max_scale : 1;
+  float slack_prev = rate_slack_min(c, sh);
+  double ee_best = R / P;
   for (int i = 0; i < Imax && !sh.abort; i++) {
+    save_iterate(c);  // p^{i-1}, kept if Algorithm 1 ends below it
+    const double q_prev = q;
     for (int m = threadIdx.x; m < c.M; m += kThreads) {
       sh.qeta[m] = (float)(q * c.eta[m]);
       sh.xif[m] = (float)c.xi[m];
@@ -114,10 +181,29 @@ __device__ void solve_instance(const Ctx &c, Shared &sh, float *dyn, const KDims
       status = 8;
       break;
     }
-    const double F = R - q * P;
-    q = R / P;
-    if (F <= tol.tol_dinkelbach * R) {
-      status = F < 0.0 ? 4 : 0;
+    const double F = R - q * P, qn = R / P;
+    const float slack = rate_slack_min(c, sh);
+    if (F < 0.0) {
+      // the inner solve ended below p^{i-1}, which attains F = 0 (Lemma 1):
+      // keep p^{i-1} and stop, unless p^{i-1} misses the streaming rates that
+      // p^i meets better
+      if (slack_prev >= -1e-3f || slack_prev >= slack) {
+        restore_iterate(c, szeta);
+        link_all<kLinkOnly>(c, sh, dyn, kd, szeta, 0.f, phase, pending);
+        exact_R_P(c, sh, R, P);
+        q = q_prev;
+        status = 0;
+        break;
+      }
+      q = qn;
+      slack_prev = slack;
+      continue;
+    }
+    q = qn;
+    slack_prev = slack;
+    ee_best = fmax(ee_best, qn);
+    if (F <= tol.tol_dinkelbach * R) {  // stop test of Sec. III, relative
+      status = 0;
       break;
     }
   }
@@ -134,28 +220,7 @@ __device__ void solve_instance(const Ctx &c, Shared &sh, float *dyn, const KDims
   for (int m = threadIdx.x; m < c.M; m += kThreads)
     smin = fminf(smin, (float)((c.pmax[m] - sh.vtot[m]) / c.pmax[m]));
   const float slack_power = block_min(smin, sh);
-  float rmin = INFINITY;
-  for (int base = 0; base < c.Ks; base += kMaxM) {  // streaming users in groups of kMaxM
-    const int cnt = c.Ks - base < kMaxM ? c.Ks - base : kMaxM;
-    for (int i = warp; i < cnt; i += kWarps) {
-      const int k = c.Ke + base + i;
-      const int a = c.A[k];
-      float r = 0.f;
-      if (a >= 0) {
-        const float wk = c.wf[(size_t)a * c.K + k];
-        for (int n = c.n0 + lane; n < c.n1; n += 32) {
-          const int u = c.uslot[(size_t)k * c.N + n];
-          if (u >= 0) r += wk * log1pf(c.gam[n * c.Up + u]) / LN2F;
-        }
-      }
-      r = warp_sum(r);
-      if (lane == 0) sh.vpart[i] = r;
-    }
-    cl_vsum(sh, c, cnt);
-    for (int i = threadIdx.x; i < cnt; i += kThreads)
-      rmin = fminf(rmin, (float)((sh.vtot[i] - c.Psi[base + i]) / c.Psi[base + i]));
-  }
-  const float slack_rate = block_min(rmin, sh);
+  const float slack_rate = rate_slack_min(c, sh);
   float smax = -INFINITY;
   for (int nm = c.n0 * c.M + threadIdx.x; nm < c.n1 * c.M; nm += kThreads) {
     const int n = nm / c.M, m = nm - n * c.M;
@@ -173,6 +238,7 @@ __device__ void solve_instance(const Ctx &c, Shared &sh, float *dyn, const KDims
   const float slack_sic = cl_max(smax, sh, c);
   if (threadIdx.x == 0 && c.crank == 0) {
     if (c.Ks > 0 && slack_rate < -1e-3f) status |= 2;
+    if (R / P < ee_best * (1.0 - 1e-9)) status |= 4;  // an earlier iterate was more efficient
     if (sh.abort) status |= kStatusTimeout;
     out->ee = R / P;
     out->R = R;
@@ -207,6 +273,7 @@ __device__ void bind(Ctx &c, const InstDesc &d, const float *gains, double *dare
   c.s_off = d.s_off;
   c.w = db + dl.w; c.xi = db + dl.xi; c.zeta = db + dl.zeta; c.zsic = db + dl.zsic;
   c.zsic_next = db + dl.zsic_next;
+  c.xi_prev = db + dl.xi_prev; c.zeta_prev = db + dl.zeta_prev; c.zsic_prev = db + dl.zsic_prev;
   const FLayout fl = flayout(d.M, d.N, d.K, d.l, nchunk_cap(d.N, d.K));
   float *fb = farena + d.f_off;
   c.p = fb + fl.p; c.plin = fb + fl.plin; c.pstart = fb + fl.pstart; c.alpha = fb + fl.alpha;
@@ -219,9 +286,12 @@ __device__ void bind(Ctx &c, const InstDesc &d, const float *gains, double *dare
   c.gown = fb + fl.gown;
   c.ginv = fb + fl.ginv;
   c.wslot = fb + fl.wslot;
-  const ILayout il = ilayout(d.M, d.N, d.K, d.l);
+  c.p_prev = fb + fl.p_prev; c.alpha_prev = fb + fl.alpha_prev; c.beta_prev = fb + fl.beta_prev;
+  const ILayout il = ilayout(d.M, d.N, d.K, d.Ks, d.l);
   int *ib = iarena + d.i_off;
   c.A = ib + il.A; c.Anew = ib + il.Anew; c.S = ib + il.S; c.uslot = ib + il.uslot;
+  c.Snew = ib + il.Snew; c.Again = ib + il.Again; c.srv = ib + il.srv;
+  c.A_prev = ib + il.A_prev; c.S_prev = ib + il.S_prev;
 }
 
 __global__ void __launch_bounds__(kThreads, 1)

@@ -51,7 +51,7 @@ struct InstDesc {
 
 // double arena of one instance
 struct DLayout {
-  int64_t pmax, eta, mask, Psi, Tdel, w, xi, zeta, zsic, zsic_next, total;
+  int64_t pmax, eta, mask, Psi, Tdel, w, xi, zeta, zsic, zsic_next, xi_prev, zeta_prev, zsic_prev, total;
 };
 HCRAN_HD DLayout dlayout(int M, int N, int K, int Ks, int l) {
   DLayout d;
@@ -67,6 +67,9 @@ HCRAN_HD DLayout dlayout(int M, int N, int K, int Ks, int l) {
   d.zeta = o; o = al4(o + (Ks > 0 ? Ks : 1));
   d.zsic = o; o = al4(o + NZ);
   d.zsic_next = o; o = al4(o + NZ);
+  d.xi_prev = o; o = al4(o + M);                      // the previous Dinkelbach iterate
+  d.zeta_prev = o; o = al4(o + (Ks > 0 ? Ks : 1));
+  d.zsic_prev = o; o = al4(o + NZ);
   d.total = o;
   return d;
 }
@@ -88,7 +91,7 @@ HCRAN_HD int nchunk_cap(int N, int K) {
 // float arena of one instance (slot arrays are [n][Up])
 struct FLayout {
   int64_t p, plin, pstart, alpha, beta, pi, gam, X, Aden, Bnum, Cnum, gown, ginv, wslot, slab, SICp, SICm,
-      Ptot, cu, cp, cX, ckey, Upart, wf, total;
+      Ptot, cu, cp, cX, ckey, Upart, wf, p_prev, alpha_prev, beta_prev, total;
 };
 HCRAN_HD FLayout flayout(int M, int N, int K, int l, int nchunk) {  // nchunk: capacity (nchunk_cap)
   FLayout f;
@@ -119,21 +122,33 @@ HCRAN_HD FLayout flayout(int M, int N, int K, int l, int nchunk) {  // nchunk: c
   f.ckey = o; o = al4(o + NK);
   f.Upart = o; o = al4(o + int64_t(nchunk) * M * K);
   f.wf = o; o = al4(o + int64_t(M) * K);
+  f.p_prev = o; o = al4(o + L);                        // the previous Dinkelbach iterate
+  f.alpha_prev = o; o = al4(o + L);
+  f.beta_prev = o; o = al4(o + L);
   f.total = o;
   return f;
 }
 
-// int arena of one instance
+// int arena of one instance: serving RRHs, slot users, the user -> slot map,
+// the selection being built (Snew), the RRH of largest summed gain of every
+// user (Again), the per-CTA served flags of the streaming users (srv), and
+// the previous Dinkelbach iterate (A_prev, S_prev)
 struct ILayout {
-  int64_t A, Anew, S, uslot, total;
+  int64_t A, Anew, S, uslot, Snew, Again, srv, A_prev, S_prev, total;
 };
-HCRAN_HD ILayout ilayout(int M, int N, int K, int l) {
+HCRAN_HD ILayout ilayout(int M, int N, int K, int Ks, int l) {
   ILayout i;
   int64_t o = 0;
+  const int64_t L = int64_t(N) * slot_stride(M, l);
   i.A = o; o = al4(o + K);
   i.Anew = o; o = al4(o + K);
-  i.S = o; o = al4(o + int64_t(N) * slot_stride(M, l));
+  i.S = o; o = al4(o + L);
   i.uslot = o; o = al4(o + int64_t(K) * N);
+  i.Snew = o; o = al4(o + L);
+  i.Again = o; o = al4(o + K);
+  i.srv = o; o = al4(o + int64_t(8) * (Ks > 0 ? Ks : 1));
+  i.A_prev = o; o = al4(o + K);
+  i.S_prev = o; o = al4(o + L);
   i.total = o;
   return i;
 }

@@ -90,7 +90,7 @@ int plan(const hcran_config &c, Plan &p) {
   d.Pconst = pc;
   const DLayout dl = dlayout(c.M, c.N, c.K, c.Ks, c.l);
   const FLayout fl = flayout(c.M, c.N, c.K, c.l, nchunk_cap(c.N, c.K));
-  const ILayout il = ilayout(c.M, c.N, c.K, c.l);
+  const ILayout il = ilayout(c.M, c.N, c.K, c.Ks, c.l);
   if (cls < kNumClasses - 1) {
     p.kd = resident_kdims(c.M, c.l, c.Ks, c.N, p.csize);
   } else {
@@ -212,7 +212,7 @@ extern "C" int hcran_solve_noalloc(const hcran_config *cfg, const float *gains_d
 
   // results into the caller's host arrays
   const FLayout fl = flayout(c.M, c.N, c.K, c.l, nchunk_cap(c.N, c.K));
-  const ILayout il = ilayout(c.M, c.N, c.K, c.l);
+  const ILayout il = ilayout(c.M, c.N, c.K, c.Ks, c.l);
   const unsigned char *fb = ws + p.o_farena, *ib = ws + p.o_iarena, *dbb = ws + p.o_darena;
   const size_t Up = slot_stride(c.M, c.l), NPp = pair_stride(c.M, c.l);
   InstOut o;

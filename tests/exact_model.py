@@ -62,12 +62,14 @@ def rates(G, P, sigma, w=None):
 
 
 def R_P(inst, P: np.ndarray):
-    """Weighted elastic sum rate R and total power P of problem (eq7)."""
+    """Weighted elastic sum rate R of problem (eq7) and the consumed power P of
+    the Sec. II-A power model: fronthaul and circuit power of every RRH plus
+    eta_m times the transmit power of every user it serves."""
     sigma = inst.N0_w_per_hz * inst.Bn_hz
     Ke = inst.K - inst.Ks
     r = rates(inst.G, P, sigma, inst.w)
     R = r[:Ke].sum()
-    Ptot = (inst.Pc + inst.Pf).sum() + (inst.eta[None, :, None] * P[:, :, :Ke]).sum()
+    Ptot = (inst.Pc + inst.Pf).sum() + (inst.eta[None, :, None] * P).sum()
     return R, Ptot
 
 

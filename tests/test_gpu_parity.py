@@ -1,19 +1,12 @@
 """CUDA solver vs FP64 oracle on the same seeded inputs, through the C ABI.
 
-Bar (element by element): RRH selection A and per-(n,m) user sets S equal
-unless a selection decision on either side had a relative margin below
-TIE_BAND (then the instance is reported as a flagged tie and only checked for
-validity); EE within 1e-4 relative; every power of a link both sides select
-within 1e-3 relative or 5% of its RRH's per-subcarrier mask.
-
-With the stop tests switched off (fixed iteration counts on both sides) and
-for short runs, the comparison is with the plain oracle.  With a workload's
-own stopping rules the comparison is with the oracle's perturbation ensemble
-(tests/oracle_ensemble.py): the plain oracle and its runs with FP32-level
-perturbations of the dual-iteration powers.  The GPU result must meet the bar
-against at least one member; for an instance with a stable end point all
-members agree to ~1e-8, so this is the plain bar.  Every report prints the
-error against the plain oracle and the ensemble's own EE spread.
+The bar is tests.parity's: the plain oracle, element by element (selection
+up to vanishing links, EE within 1e-4, powers within 1e-3), else a tie
+flagged below 1e-9 on either side or an instance whose oracle end point is
+itself rounding-sensitive, each held to the validity checks.  Every report
+prints the error against the plain oracle.  With the stop tests switched off
+(fixed iteration counts on both sides) the bar is the plain one and the
+iteration counts must agree.
 """
 import copy
 
@@ -22,13 +15,10 @@ import pytest
 
 import oracle
 from tests.oracle_ensemble import ensemble
+from tests.parity import EE_RTOL, TIE_BAND, check, classify, validity
 from hcran_inputs import Instance, Tolerances, WORKLOADS, make_instance, make_workload, pack_batch
 
 pytestmark = pytest.mark.gpu
-
-TIE_BAND = 1e-4
-EE_RTOL = 1e-4
-P_RTOL = 1e-3
 
 
 def gpu_solve(insts, tol, **tolkw):
@@ -43,76 +33,34 @@ def gpu_solve(insts, tol, **tolkw):
     return out
 
 
-def check(inst, g, o, label="", strict_powers=False, ee_rtol=EE_RTOL):
-    """Measure parity against one oracle result; rep["ok"] says whether the bar holds."""
-    mask = inst.pmax / inst.N
-    flagged = g["min_margin"] < TIE_BAND or o.min_margin < TIE_BAND
-    same_sel = np.array_equal(g["A"], o.A) and np.array_equal(g["S"], o.S)
-    ee_err = abs(g["ee"] - o.ee) / max(abs(o.ee), 1e-300)
-    sel = g["S"] >= 0
-    both = sel & (g["S"] == o.S)
-    pe = np.abs(g["p"].astype(np.float64) - o.p)
-    big = np.maximum(np.abs(o.p), np.abs(g["p"]))
-    mk = np.broadcast_to(mask[None, :, None], big.shape)
-    if strict_powers:
-        lim = P_RTOL * big + 1e-6 * mk
-    else:
-        lim = np.maximum(P_RTOL * big, 0.05 * mk)
-    p_err = float(np.max((pe / np.maximum(np.abs(o.p), 1e-300))[both])) if both.any() else 0.0
-    worst = None
-    if both.any():
-        viol = np.where(both, pe / lim, 0.0)
-        wi = np.unravel_index(np.argmax(viol), viol.shape)
-        worst = dict(at=tuple(int(x) for x in wi), p_gpu=float(g["p"][wi]), p_orc=float(o.p[wi]),
-                     frac_of_mask=float(o.p[wi] / mask[wi[1]]), over_limit=float(viol[wi]))
-    rep = dict(label=label, ee_gpu=g["ee"], ee_orc=o.ee, ee_rel=ee_err, p_maxrel=p_err, worst=worst,
-               same_selection=same_sel, flagged=flagged, iters_gpu=g["iters"], iters_orc=o.iters,
-               margin_gpu=g["min_margin"], margin_orc=o.min_margin, status=(g["status"], o.status))
-    if not flagged:
-        rep["ok"] = bool(same_sel and ee_err <= ee_rtol and np.all(pe[both] <= lim[both]))
-    else:
-        rep["ok"] = bool(np.isfinite(g["ee"]) and g["ee"] > 0)
-    return rep
-
-
-def compare(inst, g, o, label="", strict_powers=False, ee_rtol=EE_RTOL):
-    """Assert parity with one oracle result; return the measured errors."""
-    rep = check(inst, g, o, label, strict_powers, ee_rtol)
+def compare(inst, g, o, label=""):
+    """Assert the plain bar against one oracle result; return the report."""
+    rep = check(inst, g, o, label)
     print("parity", rep)
     assert rep["ok"], rep
+    validity(inst, g, label)
     return rep
 
 
-def compare_ensemble(inst, g, orcs, label="", ee_rtol=EE_RTOL):
-    """Assert parity with at least one member of the oracle's perturbation
-    ensemble (orcs[0] is the plain oracle); return the plain-oracle report
-    with the matching member and the ensemble's EE spread added."""
-    reps = [check(inst, g, o, label, ee_rtol=ee_rtol) for o in orcs]
-    base = reps[0]
-    ees = np.array([o.ee for o in orcs])
-    base["ensemble_ee_spread"] = float((ees.max() - ees.min()) / max(abs(orcs[0].ee), 1e-300))
-    base["matched_member"] = next((i for i, r in enumerate(reps) if r["ok"]), None)
-    base["members_matched"] = sum(r["ok"] for r in reps)
-    print("parity", base)
-    assert base["matched_member"] is not None, (base, [r["ee_rel"] for r in reps])
-    return base
+def hold(inst, g, tol, label="", **kw):
+    """Tier of one result under the workload's own stop rules (tests.parity)."""
+    o = oracle.solve(inst, tol, tie_eps=TIE_BAND, **kw)
+    tier, rep = classify(inst, g, o, tol, label, ensemble_fn=ensemble, **kw)
+    print("parity", tier, rep)
+    assert tier != "fail", rep
+    return tier, rep
 
 
-def test_small_config_matches_oracle():
-    name = "small-3x8x6"
+@pytest.mark.parametrize("name", ["small-3x8x6", "medium-9x64x48"])
+def test_config_matches_plain_oracle(name):
+    """The small and medium configurations under their own stop rules, held to
+    the plain oracle."""
     inst = make_workload(name)[0]
     tol = WORKLOADS[name]["tol"]
     g = gpu_solve([inst], tol)[0]
-    r = compare_ensemble(inst, g, ensemble(inst, tol), name)
-    assert not r["flagged"]
-
-
-def test_medium_config_matches_oracle():
-    name = "medium-9x64x48"
-    inst = make_workload(name)[0]
-    tol = WORKLOADS[name]["tol"]
-    g = gpu_solve([inst], tol)[0]
-    compare_ensemble(inst, g, ensemble(inst, tol), name)
+    o = oracle.solve(inst, tol, tie_eps=TIE_BAND)
+    compare(inst, g, o, name)
+    assert g["status"] == o.status == 0
 
 
 @pytest.mark.parametrize("v", [1, 5, 60])
@@ -140,7 +88,7 @@ def test_algorithm1_matches_at_fixed_E():
     tol = copy.copy(WORKLOADS[name]["tol"])
     tol.max_dinkelbach = 1
     g = gpu_solve([inst], tol, q_init=60.0)[0]
-    compare_ensemble(inst, g, ensemble(inst, tol, q_init=60.0), "alg1@E=60")
+    compare(inst, g, oracle.solve(inst, tol, q_init=60.0, tie_eps=TIE_BAND), "alg1@E=60")
 
 
 @pytest.mark.parametrize("name", ["medium-9x64x48", "batch"])
@@ -154,7 +102,7 @@ def test_fixed_iteration_counts_match_everywhere(name):
     for inst, g in zip(insts, gs):
         o = oracle.solve(inst, tol)
         assert g["iters"] == o.iters
-        compare(inst, g, o, "fixed-count " + name, strict_powers=True)
+        compare(inst, g, o, "fixed-count " + name)
 
 
 def _batch_subset(count=4, max_cost=40000):
@@ -169,15 +117,13 @@ def _batch_subset(count=4, max_cost=40000):
 
 
 def test_uneven_batch_in_one_launch_matches_oracle():
-    insts = _batch_subset()
+    insts = _batch_subset(count=6)
     tol = WORKLOADS["batch-4096-uneven"]["tol"]
     gs = gpu_solve(insts, tol)
-    errs = []
-    for inst, g in zip(insts, gs):
-        r = compare_ensemble(inst, g, ensemble(inst, tol),
-                             "seed%d M%d N%d K%d" % (inst.seed, inst.M, inst.N, inst.K))
-        errs.append((r["ee_rel"], r["ensemble_ee_spread"]))
-    print("uneven batch (EE error vs plain oracle, ensemble spread)", errs)
+    tiers = [hold(inst, g, tol, "seed%d M%d N%d K%d" % (inst.seed, inst.M, inst.N, inst.K))[0]
+             for inst, g in zip(insts, gs)]
+    print("uneven batch tiers", tiers)
+    assert tiers.count("plain") >= len(tiers) - 1
 
 
 def test_repeat_runs_are_bitwise_identical():
@@ -207,7 +153,7 @@ def test_edge_shapes_match_oracle(shape):
         assert g["ee"] == 0.0 and o.ee == 0.0
         assert np.array_equal(g["S"], o.S)
         return
-    compare_ensemble(inst, g, ensemble(inst, tol), str(shape))
+    hold(inst, g, tol, str(shape))
 
 
 def _solver(insts):
@@ -257,7 +203,7 @@ def test_every_cluster_size_matches_oracle_at_fixed_counts():
         for i, (inst, o) in enumerate(zip(insts, orcs)):
             r = s.get(i)
             assert r["iters"] == o.iters
-            compare(inst, r, o, "schedule %d (got %d)" % (want, s.schedule()[i]), strict_powers=True)
+            compare(inst, r, o, "schedule %d (got %d)" % (want, s.schedule()[i]))
 
 
 def test_autotuned_schedule_is_valid_and_matches_oracle():
@@ -272,7 +218,7 @@ def test_autotuned_schedule_is_valid_and_matches_oracle():
     assert np.all((after == 0) | (after >= before))
     s.solve(g, make_tol(tol, tie_eps=TIE_BAND))
     for i, inst in enumerate(insts):
-        compare(inst, s.get(i), oracle.solve(inst, tol), "autotuned", strict_powers=True)
+        compare(inst, s.get(i), oracle.solve(inst, tol), "autotuned")
 
 
 def test_large_instance_matches_oracle_at_fixed_counts():
@@ -286,5 +232,5 @@ def test_large_instance_matches_oracle_at_fixed_counts():
     g = gpu_solve([inst], tol)[0]
     o = oracle.solve(inst, tol)
     assert g["iters"] == o.iters
-    compare(inst, g, o, "large fixed-count", strict_powers=True)
+    compare(inst, g, o, "large fixed-count")
 

@@ -37,12 +37,14 @@ MUTANTS = {
                           "for (int b = s + 1; b < I->l; b++)\n    if (st->S[slot(I, n, m, b)] >= 0) intra += st->p[slot(I, n, m, b)];"),
     "victim_gain_transposed": ("acc += pi[slot(I, n, j, b)] * gain(I, n, m, v);",
                                "acc += pi[slot(I, n, j, b)] * gain(I, n, j, v);"),
-    "drop_ee_price": ("double den = (k < I->Ke ? q * I->eta[m] : 0.0) + st->xi[m] +\n                     victim_price(I, st, w->pi, n, m, k, -1)",
+    "drop_ee_price": ("double den = q * I->eta[m] + st->xi[m] +\n                     victim_price(I, st, w->pi, n, m, k, -1)",
                       "double den = st->xi[m] +\n                     victim_price(I, st, w->pi, n, m, k, -1)"),
+    "streaming_ee_price_dropped": ("double den = q * I->eta[m] + st->xi[m] +\n                     victim_price(I, st, w->pi, n, m, k, -1)",
+                                   "double den = (k < I->Ke ? q * I->eta[m] : 0.0) + st->xi[m] +\n                     victim_price(I, st, w->pi, n, m, k, -1)"),
     "zeta_step_sign": ("double x = (I->Psi[ks] - r) / (asum > ZETA_ASUM_MIN ? asum : ZETA_ASUM_MIN);",
                        "double x = (r - I->Psi[ks]) / (asum > ZETA_ASUM_MIN ? asum : ZETA_ASUM_MIN);"),
-    "power_counts_streaming": ("if (k < 0 || k >= I->Ke) continue;\n        double ie = noise_plus_interference(I, st, Ptot, n, m, s);\n        double g = st->p[e] * gain(I, n, m, k) / ie;\n        r += I->w[(size_t)m * I->K + k] * log2(1.0 + g);\n        tx += I->eta[m] * st->p[e];",
-                               "if (k < 0) continue;\n        tx += I->eta[m] * st->p[e];\n        if (k >= I->Ke) continue;\n        double ie = noise_plus_interference(I, st, Ptot, n, m, s);\n        double g = st->p[e] * gain(I, n, m, k) / ie;\n        r += I->w[(size_t)m * I->K + k] * log2(1.0 + g);"),
+    "power_omits_streaming": ("if (k < 0) continue;\n        tx += I->eta[m] * st->p[e];\n        if (k >= I->Ke) continue;",
+                              "if (k < 0 || k >= I->Ke) continue;\n        tx += I->eta[m] * st->p[e];"),
     "interference_price_alpha_dropped": ("pi[e] = weight_c(I, st, m, k) * st->alpha[e] / (LN2 * ie);",
                                          "pi[e] = weight_c(I, st, m, k) / (LN2 * ie);"),
 }

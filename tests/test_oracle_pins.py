@@ -127,11 +127,12 @@ def test_oma_single_rrh_is_waterfilling_at_fixed_E():
 
 def lagrangian(inst, P, r, E):
     """L of problem (final_Problem_formulation_1) with exact rates, using the
-    oracle's multipliers: elastic rate - E * power + rate and budget and SIC terms."""
+    oracle's multipliers: elastic rate - E * transmit power (every user, the
+    Sec. II-A power model) + rate and budget and SIC terms."""
     sigma = inst.N0_w_per_hz * inst.Bn_hz
     Ke = inst.K - inst.Ks
     rk = em.rates(inst.G, P, sigma, inst.w)
-    L = rk[:Ke].sum() - E * (inst.eta[None, :, None] * P[:, :, :Ke]).sum()
+    L = rk[:Ke].sum() - E * (inst.eta[None, :, None] * P).sum()
     if inst.Ks:
         L += np.dot(r.zeta, rk[Ke:] - em.psi(inst))
     L -= np.dot(r.xi, P.sum(axis=(0, 2)) - inst.pmax)
@@ -226,7 +227,10 @@ def test_reported_R_P_match_independent_model(name):
     assert r.R == pytest.approx(R, rel=1e-12)
     assert r.P == pytest.approx(Pt, rel=1e-12)
     assert r.ee == pytest.approx(R / Pt, rel=1e-12)
-    assert r.q_trace[-1] == pytest.approx(R / Pt, rel=1e-12)
+    # the output is the last Dinkelbach iterate, or the one before it when the
+    # last inner solve ended below it (F < 0) and was not kept
+    kept = r.q_trace[-2] if (r.F_trace[-1] < 0 and r.ee != r.q_trace[-1]) else r.q_trace[-1]
+    assert kept == pytest.approx(R / Pt, rel=1e-12)
 
 
 # ---------------------------------------------------------------- invariants
@@ -370,8 +374,9 @@ def test_oracle_not_above_brute_force(shape, seed):
     inst = micro(G, l=2, pmax=[1.0] * M, eta=[2.0] * M)
     r = oracle.solve(inst, Tolerances())
     bf = brute_force_ee(inst)
+    print(shape, "oracle", r.ee, "brute force", bf)
     assert r.ee <= bf * (1 + 1e-3)
-    assert r.ee >= 0.5 * bf
+    assert r.ee >= 0.99 * bf
 
 
 # micro versions (one subcarrier, three elastic users) of the architectures of
@@ -390,9 +395,10 @@ _MICRO_ARCH = {
 @pytest.mark.parametrize("arch", sorted(_MICRO_ARCH))
 def test_oracle_not_above_brute_force_on_micro_architectures(arch):
     """The brute-force bound on micro versions of every architecture the
-    paper compares: the oracle cannot beat it and stays close to it (measured:
-    99.3-100 % under PD-NOMA, 90 % under OMA, where the method stops in a
-    local optimum)."""
+    paper compares: the oracle cannot beat it and stays close to it, as the
+    paper states for its solution (Sec. VI): at least 99 % of the optimum under
+    PD-NOMA (measured 99.3-100 %) and 85 % under OMA (measured 89.6 %, a local
+    optimum with one user per subcarrier)."""
     from hcran_inputs import make_instance
     a = _MICRO_ARCH[arch]
     inst = make_instance(700000, M=a["M"], N=1, K=3, Ks=0, l=a["l"], layout=a["layout"], per_rrh=a["per_rrh"])
@@ -400,7 +406,7 @@ def test_oracle_not_above_brute_force_on_micro_architectures(arch):
     bf = brute_force_ee(inst, starts=3, sweeps=8)
     print(arch, "oracle", r.ee, "brute force", bf)
     assert r.ee <= bf * (1 + 1e-3)
-    assert r.ee >= 0.5 * bf
+    assert r.ee >= (0.85 if a["l"] == 1 else 0.99) * bf
 
 
 def test_perturbation_ensemble_is_opt_in_and_small_on_a_stable_instance():

@@ -51,72 +51,32 @@ def test_oracle_solution_meets_the_constraints(name):
         assert np.isfinite(o.ee) and o.ee > 0.0
 
 
-def _sensitivity_bar(inst, tol, g, o, label):
-    """Weaker bar for an instance whose end point moves under rounding (seen
-    under OMA, where every instance leaves some streaming user unmet and one
-    link sits on a clip boundary of the dual iteration): the tolerance-driven
-    bar against the plain oracle (EE within 1e-4, powers within max(1e-3
-    relative, 5% of the mask)), or, when the oracle's own EE moves, the
-    oracle's perturbation ensemble at 2^-22 (the GPU's fast reciprocal and
-    hardware log2 are within 2 ulp; 15 members) spreading by more than the
-    1e-4 EE bar and the GPU EE within the ensemble's range widened by that
-    spread. Returns (ok, message)."""
-    from tests.oracle_ensemble import ensemble
-    from tests.test_gpu_parity import check
-    if check(inst, g, o, label)["ok"]:
-        return True, label + ": within the tolerance-driven bar"
-    ees = np.array([o.ee for o in ensemble(inst, tol, n=15, noise_rel=2.0 ** -22)])
-    lo, hi = ees.min(), ees.max()
-    spread = hi - lo
-    ok = spread > 1e-4 * abs(ees[0]) and lo - spread <= g["ee"] <= hi + spread
-    return ok, "%s: gpu ee %.6f, ensemble %.6f .. %.6f (spread %.2e)" % (label, g["ee"], lo, hi, spread / abs(ees[0]))
-
-
 @pytest.mark.gpu
 def test_scenarios_match_oracle_at_fixed_counts():
-    """Stop tests off: the strict bar of the batch workloads, or, on an
-    instance whose end point the oracle's own rounding moves, the weaker bar
-    of `_sensitivity_bar`."""
-    from tests.test_gpu_parity import check, gpu_solve
+    """Stop tests off (every loop runs to its cap): the plain bar, with the
+    same iteration counts on both sides, on three instances of every
+    architecture."""
+    from tests.test_gpu_parity import compare, gpu_solve
     tol = Tolerances(tol_dinkelbach=0.0, tol_scale=0.0, tol_dual=0.0, max_dinkelbach=2, max_scale=3, max_dual=40)
-    strict, weak, failed = [], [], []
     for name in SCENARIOS:
         insts = make_workload(name, count=3)
         for inst, g in zip(insts, gpu_solve(insts, tol)):
             o = oracle.solve(inst, tol)
-            label = "fixed-count %s seed %d" % (name, inst.seed)
-            rep = check(inst, g, o, label, strict_powers=True)
-            print("parity", rep)
-            if g["iters"] == o.iters and rep["ok"]:
-                strict.append(label)
-                continue
-            ok, msg = _sensitivity_bar(inst, tol, g, o, label)
-            print("sensitive", msg)
-            (weak if ok and rep["same_selection"] else failed).append(msg)
-    print("strict", len(strict), "weak", weak, "failed", failed)
-    assert not failed, failed
-    assert len(strict) >= 12, (strict, weak)
+            assert g["iters"] == o.iters
+            compare(inst, g, o, "fixed-count %s seed %d" % (name, inst.seed))
 
 
 @pytest.mark.gpu
-def test_scenarios_match_oracle_ensemble():
-    """With the workloads' own stop rules: a member of the oracle's 2^-24
-    ensemble within the bar, or the weaker bar of `_sensitivity_bar`."""
-    from tests.oracle_ensemble import ensemble
-    from tests.test_gpu_parity import check, gpu_solve
-    weak, failed = [], []
+def test_scenarios_match_oracle_under_their_stop_rules():
+    """With the workloads' own stop rules, three instances of every
+    architecture held to the tiers of tests.parity; at most one of the fifteen
+    may fall outside the plain bar."""
+    from tests.test_gpu_parity import gpu_solve, hold
+    tiers = []
     for name in SCENARIOS:
         tol = WORKLOADS[name]["tol"]
-        insts = make_workload(name, count=2)
+        insts = make_workload(name, count=3)
         for inst, g in zip(insts, gpu_solve(insts, tol)):
-            orcs = ensemble(inst, tol, n=15)
-            label = "%s seed %d" % (name, inst.seed)
-            reps = [check(inst, g, o, label) for o in orcs]
-            print("parity", reps[0], "members matched", sum(r["ok"] for r in reps))
-            if any(r["ok"] for r in reps):
-                continue
-            ok, msg = _sensitivity_bar(inst, tol, g, orcs[0], label)
-            print("sensitive", msg)
-            (weak if ok else failed).append(msg)
-    print("weak", weak, "failed", failed)
-    assert not failed, failed
+            tiers.append(hold(inst, g, tol, "%s seed %d" % (name, inst.seed))[0])
+    print("scenario tiers", tiers)
+    assert tiers.count("plain") >= len(tiers) - 1, tiers
