@@ -23,10 +23,16 @@ PIN_SET = [
     pins.test_kkt_two_interfering_links,
     pins.test_kkt_noma_pair_same_rrh,
     pins.test_kkt_with_streaming_user,
+    lambda: pins.test_kkt_sic_multiplier_across_rrhs(300, 1),
+    lambda: pins.test_kkt_sic_multiplier_across_rrhs(1054, 2),
     lambda: pins.test_reported_R_P_match_independent_model("small-3x8x6"),
 ]
 
 MUTANTS = {
+    "sic_split_swapped": ("if (c > 0.0) sp += z * c;\n            else sm += z * (-c);",
+                          "if (c < 0.0) sp += z * (-c);\n            else sm += z * c;"),
+    "sic_coefficient_transposed": ("double c = gain(I, n, j, ka) / gain(I, n, m, ka) - gain(I, n, j, kb) / gain(I, n, m, kb);",
+                                   "double c = gain(I, n, m, ka) / gain(I, n, j, ka) - gain(I, n, m, kb) / gain(I, n, j, kb);"),
     "psi_larger_root": ("double psi_hat = 2.0 * lambda_pps * zbar_bits / (b - root);",
                         "double psi_hat = 2.0 * lambda_pps * zbar_bits / (b + root);"),
     "scale_beta_sign": ("*beta = log2(1.0 + z0) - a * log2(z0);",

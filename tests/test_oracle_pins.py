@@ -215,6 +215,57 @@ def test_kkt_with_streaming_user():
     assert rk[2] >= em.psi(inst)[0] * (1 - 1e-5)
 
 
+def sic_family(trial, seed=0):
+    """Three RRHs on one subcarrier: RRH 0 serves a NOMA pair (users 0, 1),
+    RRH 1 and RRH 2 one user each.  RRH 1 reaches RRH 0's stronger user
+    relatively more than its weaker one (a positive coefficient of P_1 in
+    Omega_bar of the pair: priced in RRH 1's denominator), RRH 2 the reverse
+    (a negative coefficient: RRH 2's numerator term of the DC step).  Draw
+    number `trial` of a seeded stream; returns (G, E, pmax)."""
+    rng = np.random.default_rng(seed)
+    for t in range(trial + 1):
+        G = np.zeros((1, 3, 4))
+        ga = 10 ** rng.uniform(-12.5, -11.5)
+        gb = ga * 10 ** rng.uniform(-1.0, -0.2)
+        G[0, 0, 0], G[0, 0, 1] = ga, gb
+        G[0, 1, 2] = 10 ** rng.uniform(-12.5, -11.5)
+        G[0, 2, 3] = 10 ** rng.uniform(-12.5, -11.5)
+        G[0, 1, 0] = ga * 10 ** rng.uniform(-2.5, -0.8)
+        G[0, 1, 1] = gb * 10 ** rng.uniform(-4.5, -2.5)
+        G[0, 2, 0] = ga * 10 ** rng.uniform(-4.5, -2.5)
+        G[0, 2, 1] = gb * 10 ** rng.uniform(-2.5, -0.8)
+        G[0, 0, 2] = G[0, 1, 2] * 10 ** rng.uniform(-4, -2)
+        G[0, 2, 2] = G[0, 1, 2] * 10 ** rng.uniform(-4, -2)
+        G[0, 0, 3] = G[0, 2, 3] * 10 ** rng.uniform(-4, -2)
+        G[0, 1, 3] = G[0, 2, 3] * 10 ** rng.uniform(-4, -2)
+        pm = float(10 ** rng.uniform(-0.5, 1.0))
+        E = float(10 ** rng.uniform(-1.5, 1))
+    return G.astype(np.float32), E, pm
+
+
+@pytest.mark.parametrize("trial,priced", [(300, 1), (1054, 2)])
+def test_kkt_sic_multiplier_across_rrhs(trial, priced):
+    """C14 active across RRHs (sic_terms): RRH 0's NOMA pair is held at the
+    SIC boundary by the power of the other RRHs, so its multiplier zeta_sic'
+    is positive and enters the KKT powers of RRH 1 (denominator, positive
+    coefficient) and RRH 2 (numerator, negative coefficient).  At the
+    converged point the exact Lagrangian is stationary in every interior
+    power, including the power of RRH `priced`, whose derivative carries the
+    multiplier; a swapped split of the coefficients breaks that."""
+    G, E, pm = sic_family(trial)
+    inst = micro(G, l=2, pmax=[pm] * 3, eta=[2.0] * 3)
+    r = oracle.solve(inst, TIGHT, q_init=E, max_dinkelbach=1)
+    assert list(r.A) == [0, 0, 1, 2]
+    assert list(r.S[0, 0]) == [0, 1] and r.S[0, 1, 0] == 2 and r.S[0, 2, 0] == 3
+    assert r.zeta_sic[0, 0, 0] > 0
+    P = em.dense_power(r.S, r.p, inst.K)
+    om = em.omega_bar(inst, P, 0, 0, 0, 1)
+    assert abs(om) <= 1e-6 * (SIGMA / float(G[0, 0, 1]))      # complementary slackness: C14 binds
+    p_pr = r.p[0, priced, 0]
+    assert 1e-6 * pm < p_pr < pm * (1 - 1e-9)                  # the priced RRH's power is interior
+    assert check_stationary(inst, r, E, rtol=1e-4) >= 3
+
+
 # ---------------------------------------------------------------- exact R, P, EE
 
 @pytest.mark.parametrize("name", ["small-3x8x6", "scenario-hcran-oma", "scenario-cran-1tier", "scenario-hcn-2tier",
