@@ -246,16 +246,17 @@ void hcran_destroy(hcran_t h);
  *  - gains_dev: float32 Gamma[n][m][k], device memory, 16-byte aligned.
  *  - out: caller-allocated host arrays as in hcran_result (NULL skips one).
  *  - Enqueues on `stream`, then synchronises it and copies the results; the
- *    call returns when they are in `out`.
- *  - The first call on a device looks up the array's device address with
- *    that device current; make that first call before any stream capture.
+ *    call returns when they are in `out`.  Because it synchronises and
+ *    copies synchronously, it cannot run inside a stream capture.
+ *  - Every call looks up the array's address on the current device.
  *  - Every call on a device reuses the same array and leaves the previous
  *    call's contents behind; the call initialises everything it reads.  Two
  *    calls whose work overlaps on one GPU (different streams or threads)
  *    race on the array: serialise them.
  *  - Returns HCRAN_E2BIG, without touching the GPU, when the instance's
- *    workspace exceeds the array (about M*N*(23*M*l + 12*K) + 30*N*M*l bytes
- *    must stay under 16 MiB); HCRAN_EINVAL for a bad config or tolerance. */
+ *    workspace exceeds the array (about 4*N*M*M*l + 92*N*M*l + 20*N*K +
+ *    12*N*M*l*(l-1) bytes must stay under 16 MiB); HCRAN_EINVAL for a bad
+ *    config or tolerance. */
 #define HCRAN_NOALLOC_SCRATCH_BYTES (16u << 20)
 int hcran_solve_noalloc(const hcran_config *cfg, const float *gains_dev, const hcran_tol *tol, void *stream,
                         hcran_result *out);

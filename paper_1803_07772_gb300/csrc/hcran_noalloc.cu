@@ -10,8 +10,8 @@
 // from one file-scope device array instead of a caller-provided workspace.
 //
 // The array below is part of the module: every GPU that loads this library
-// keeps it (kNoallocScratchBytes) until the process exits.  Its device address
-// is looked up once per device, by the first call made on that device.
+// keeps it (kNoallocScratchBytes) until the process exits.  Every call looks
+// up its device address on the current device.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <string.h>
@@ -31,15 +31,13 @@ using namespace hcran;
 namespace {
 
 constexpr size_t kNoallocScratchBytes = size_t(HCRAN_NOALLOC_SCRATCH_BYTES);
-constexpr int kMaxDevices = 64;
 
 // The solver's whole workspace for hcran_solve_noalloc.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
 
-// Device address of g_noalloc_scratch per device; filled by the first call on
-// that device (with that device current).  In host code the name of the
-// array is only a host-side stand-in, never a usable device pointer.
-static void *g_scratch_dev[kMaxDevices];
+// In host code the name of the array is only a host-side stand-in, never a
+// usable device pointer: every call asks cudaGetSymbolAddress for the array's
+// address on the current device.
 
 struct Plan {
   InstDesc d;
@@ -157,15 +155,12 @@ extern "C" int hcran_solve_noalloc(const hcran_config *cfg, const float *gains_d
   rc = plan(*cfg, p);
   if (rc != HCRAN_OK) return rc;
 
-  // set-up, once per device: the device address of the static array
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return HCRAN_ECUDA;
-  if (!g_scratch_dev[dev]) {
-    void *ptr = nullptr;
-    if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) return HCRAN_ECUDA;
-    g_scratch_dev[dev] = ptr;
-  }
-  unsigned char *ws = static_cast<unsigned char *>(g_scratch_dev[dev]);
+  // the device address of the static array on the current device, looked up
+  // on every call (cheap), so that a re-created context or another current
+  // device is always served from its own copy
+  void *ptr = nullptr;
+  if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) return HCRAN_ECUDA;
+  unsigned char *ws = static_cast<unsigned char *>(ptr);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const hcran_config &c = *cfg;
   const DLayout dl = dlayout(c.M, c.N, c.K, c.Ks, c.l);

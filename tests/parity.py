@@ -8,8 +8,11 @@ Test infrastructure only.  An instance meets the bar in one of three ways:
     on every (n, m) the same users, apart from vanishing links (present on one
     side only and carrying less than ``VANISH`` of the RRH's mask, so they
     move neither R nor P beyond rounding); EE within ``EE_RTOL``; every power
-    of a link both sides select within ``P_RTOL`` relative (plus 1e-6 of the
-    mask for powers near the floor).
+    of a link both sides select within ``P_RTOL`` relative, plus an absolute
+    allowance for powers far below the mask: 1e-6 of the mask when both
+    sides run the same iteration counts, else the dual loop's own stopping
+    tolerance varpi_1 (the method fixes a power only to max |dp| / mask <
+    varpi_1, so two runs that stop one iteration apart differ by that much).
 
 ``tie``
     A selection decision on either side had a relative margin below
@@ -63,9 +66,10 @@ def selection_diff(inst, g, o):
     return (not a_diff and not differ), dict(a_diff=a_diff[:8], link_diff=differ[:8], vanishing=vanishing)
 
 
-def power_error(inst, g, o):
+def power_error(inst, g, o, p_abs=1e-6):
     """Max relative error of the powers of links both sides select, and the
-    worst link's excess over the bar (<= 1 passes)."""
+    worst link's excess over the bar (<= 1 passes); p_abs is the absolute
+    allowance in units of the mask."""
     mask = inst.pmax / inst.N
     worst, excess = 0.0, 0.0
     for n in range(inst.N):
@@ -73,18 +77,20 @@ def power_error(inst, g, o):
             lg, lo = _links(g["S"], g["p"], n, m), _links(o.S, o.p, n, m)
             for k in lg.keys() & lo.keys():
                 a, b = lg[k], lo[k]
-                lim = P_RTOL * max(a, b) + 1e-6 * mask[m]
+                lim = P_RTOL * max(a, b) + p_abs * mask[m]
                 worst = max(worst, abs(a - b) / max(b, 1e-300))
                 excess = max(excess, abs(a - b) / lim)
     return worst, excess
 
 
-def validity(inst, r, label=""):
+def validity(inst, r, label="", ref=None):
     """The result on its own: C1 (at most l distinct users per (n, m), packed,
     in SIC order), C5 (a user only on its RRH), C4 (0 < p <= mask), C12
-    after the projection, C14 in divided form (max Omega_bar / mask), the
-    streaming status bit against the reported slack, and the reported EE
-    against R / P recomputed from S and p by the independent model."""
+    after the projection, C14 in divided form (max Omega_bar / mask: the
+    multiplier method enforces it in the limit, so it is held to 1e-2, or to
+    the oracle result `ref`'s own value plus 1e-2), the streaming status bit
+    against the reported slack, and the reported EE against R / P recomputed
+    from S and p by the independent model."""
     S, p, A = np.asarray(r["S"]), np.asarray(r["p"], dtype=np.float64), np.asarray(r["A"])
     N, M, l = S.shape
     mask = inst.pmax / inst.N
@@ -101,7 +107,8 @@ def validity(inst, r, label=""):
                 assert 0.0 < p[n, m, s] <= mask[m] * (1 + 1e-6), (label, "C4", n, m, s)
     P = em.dense_power(S, p, inst.K)
     assert np.all(P.sum(axis=(0, 2)) <= inst.pmax * (1 + 1e-5)), (label, "C12")
-    assert r["slack_sic_max"] < 1e-2, (label, "C14", r["slack_sic_max"])
+    sic_bar = 1e-2 + (max(ref.slack_sic_max, 0.0) if ref is not None else 0.0)
+    assert r["slack_sic_max"] < sic_bar, (label, "C14", r["slack_sic_max"], sic_bar)
     if inst.Ks:
         assert bool(r["status"] & 2) == (r["slack_rate_min"] < -1e-3), (label, "status vs C13 slack")
     R, Pt = em.R_P(inst, P)
@@ -109,11 +116,11 @@ def validity(inst, r, label=""):
     assert abs(r["ee"] - R / Pt) <= 1e-5 * max(R / Pt, 1e-12), (label, "EE vs model", r["ee"], R / Pt)
 
 
-def check(inst, g, o, label=""):
+def check(inst, g, o, label="", p_abs=1e-6):
     """Plain-bar report of one result against one oracle result."""
     same, sel = selection_diff(inst, g, o)
     ee_err = abs(g["ee"] - o.ee) / max(abs(o.ee), 1e-300)
-    p_err, p_excess = power_error(inst, g, o)
+    p_err, p_excess = power_error(inst, g, o, p_abs)
     rep = dict(label=label, ee_gpu=g["ee"], ee_orc=o.ee, ee_rel=ee_err, p_maxrel=p_err, p_excess=p_excess,
                same_selection=same, sel=sel, margin_gpu=g["min_margin"], margin_orc=o.min_margin,
                status=(g["status"], o.status), iters_gpu=tuple(g["iters"]), iters_orc=tuple(o.iters))
@@ -123,10 +130,11 @@ def check(inst, g, o, label=""):
 
 def classify(inst, g, o, tol, label="", ensemble_fn=None, **solve_kw):
     """Tier of one result: 'plain', 'tie', 'sensitive' or 'fail', with the report."""
-    rep = check(inst, g, o, label)
+    rep = check(inst, g, o, label, p_abs=max(1e-6, tol.tol_dual))
     if rep["ok"]:
+        validity(inst, g, label, ref=o)
         return "plain", rep
-    validity(inst, g, label)
+    validity(inst, g, label, ref=o)
     if min(g["min_margin"], o.min_margin) < TIE_BAND:
         return "tie", rep
     if ensemble_fn is not None:

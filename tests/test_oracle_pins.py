@@ -284,6 +284,19 @@ def test_reported_R_P_match_independent_model(name):
     assert kept == pytest.approx(R / Pt, rel=1e-12)
 
 
+@pytest.mark.parametrize("name", ["small-3x8x6", "medium-9x64x48", "scenario-hcran-noma", "scenario-hcran-oma",
+                                  "scenario-hpn-1tier"])
+def test_oracle_results_pass_the_validity_checks(name):
+    """The validity checks the parity tests apply to non-plain CUDA results
+    (tests.parity.validity), run on the oracle's own results."""
+    from tests.parity import validity
+    inst = make_workload(name)[0]
+    r = oracle.solve(inst, WORKLOADS[name]["tol"])
+    d = dict(S=r.S, p=r.p, A=r.A, ee=r.ee, status=r.status, slack_rate_min=r.slack_rate_min,
+             slack_sic_max=r.slack_sic_max)
+    validity(inst, d, name)
+
+
 # ---------------------------------------------------------------- invariants
 
 def structural_checks(inst, r):
