@@ -1,7 +1,7 @@
 """The parity bar between a CUDA result and the FP64 oracle, and the validity
 checks that every result must pass on its own.
 
-Test infrastructure only.  An instance meets the bar in one of three ways:
+Test infrastructure only.  An instance meets the bar in one of four ways:
 
 ``plain``
     Against the plain oracle: the RRH choice A_k equal for every served user;
@@ -19,6 +19,15 @@ Test infrastructure only.  An instance meets the bar in one of three ways:
     ``TIE_BAND`` (1e-9, the band of the target precision): the two sides may
     break the tie differently.  The result must pass ``validity`` and its EE
     error is reported.
+
+``stop``
+    A tolerance-driven stop test (the dual loop's varpi_1, the SCALE loop's
+    varpi_2, the Dinkelbach test) fired at a different iteration on the two
+    sides, so the iteration counts differ: the two end points then differ by
+    the tolerance in the directions the method resolves slowly (powers far
+    below the mask), which later selections can turn into a different link
+    of small power.  The EE must still be within ``EE_RTOL`` of the plain
+    oracle, and the result must pass ``validity``.
 
 ``sensitive``
     The oracle's own end point moves under FP32-level rounding: its
@@ -129,7 +138,7 @@ def check(inst, g, o, label="", p_abs=1e-6):
 
 
 def classify(inst, g, o, tol, label="", ensemble_fn=None, **solve_kw):
-    """Tier of one result: 'plain', 'tie', 'sensitive' or 'fail', with the report."""
+    """Tier of one result: 'plain', 'tie', 'stop', 'sensitive' or 'fail', with the report."""
     rep = check(inst, g, o, label, p_abs=max(1e-6, tol.tol_dual))
     if rep["ok"]:
         validity(inst, g, label, ref=o)
@@ -137,6 +146,8 @@ def classify(inst, g, o, tol, label="", ensemble_fn=None, **solve_kw):
     validity(inst, g, label, ref=o)
     if min(g["min_margin"], o.min_margin) < TIE_BAND:
         return "tie", rep
+    if tuple(g["iters"]) != tuple(o.iters) and rep["ee_rel"] <= EE_RTOL:
+        return "stop", rep
     if ensemble_fn is not None:
         ees = np.array([x.ee for x in ensemble_fn(inst, tol, **solve_kw)])
         spread = float((ees.max() - ees.min()) / max(abs(ees[0]), 1e-300))
