@@ -144,6 +144,29 @@ int hcran_get(hcran_t h, int32_t index, hcran_result *out);
 int hcran_get_summary(hcran_t h, double *ee, double *R, double *P, int32_t *status,
                       int32_t *iters3, double *min_margin, int32_t *n_ties);
 
+/* Start point of instance `index` for the next hcran_solve / hcran_solve_host
+ * (Sec. III: iteration i of the Dinkelbach method starts from p^{i-1} and its
+ * multipliers; the outer iteration eq. outer_iterative_algorithm carries them
+ * from one iteration to the next).  The next solve starts that instance from
+ * `state` (the allocation A, S, p of a hcran_result, as hcran_get returns it,
+ * with E^1 = R(p)/P(p)) instead of the cold initial point; the other
+ * instances start cold.  Exporting the state of a solve stopped by its
+ * Dinkelbach cap (hcran_get) and importing it here continues that solve:
+ * the continued solve takes the same steps as an uninterrupted one.
+ *  - workspace_dev: the workspace the next solve will use.
+ *  - state: host arrays read during the call only; A, S and p are required;
+ *    alpha, beta (default 1, 0), xi (0), zeta (1) and zeta_sic (0) may be NULL.
+ *  - The state must be an allocation: A_k in [-1, M); on every (n, m) at
+ *    most l distinct users, each with A_k = m, packed at the front (-1
+ *    after them), in SIC order; powers in [0, pmax_m / N]; xi, zeta_sic >= 0
+ *    and zeta in [1e-6, 1e6], all finite.  Otherwise HCRAN_EINVAL and
+ *    nothing is written.
+ *  - The copies are enqueued on `stream` (pageable sources, staged before
+ *    the call returns).  The state applies to one solve; hcran_solve_graph
+ *    and hcran_autotune return HCRAN_EINVAL while a state is pending.
+ *  - HCRAN_ECUDA if a copy fails. */
+int hcran_set_state(hcran_t h, void *workspace_dev, int32_t index, const hcran_result *state, void *stream);
+
 /* Per-instance SM clock cycles spent in each phase of the last solve
  * (cycles[8*b + i]: 0 selection, 1 interference/SINR/prices, 2 multiplier
  * steps, 3 KKT power update, 4 SCALE coefficient update, 5 projection and

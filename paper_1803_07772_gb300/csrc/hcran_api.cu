@@ -366,13 +366,121 @@ static int do_solve(hcran_t h, const float *gains_dev, const hcran_tol *tol, voi
   return err == cudaSuccess ? HCRAN_OK : HCRAN_ECUDA;
 }
 
+// a state set by hcran_set_state applies to one solve: once the descriptors
+// that carry it are enqueued, the host copies go back to the cold start
+static void clear_start_flags(hcran_t h) {
+  bool any = false;
+  for (InstDesc &d : h->descs)
+    if (d.start) {
+      d.start = 0;
+      any = true;
+    }
+  if (any) h->plan_dirty = true;
+}
+static bool start_pending(hcran_t h) {
+  for (const InstDesc &d : h->descs)
+    if (d.start) return true;
+  return false;
+}
+
 extern "C" int hcran_solve(hcran_t h, const float *gains_dev, const hcran_tol *tol,
                            void *workspace_dev, void *stream) {
   if (!h || !gains_dev || !ws_ok(workspace_dev) || (reinterpret_cast<uintptr_t>(gains_dev) & 15))
     return HCRAN_EINVAL;
   const int rc = check_tol(tol);
   if (rc != HCRAN_OK) return rc;
-  return do_solve(h, gains_dev, tol, workspace_dev, stream);
+  const int r = do_solve(h, gains_dev, tol, workspace_dev, stream);
+  clear_start_flags(h);
+  return r;
+}
+
+extern "C" int hcran_set_state(hcran_t h, void *workspace_dev, int32_t index, const hcran_result *st,
+                               void *stream) {
+  if (!h || !ws_ok(workspace_dev) || !st || index < 0 || index >= h->n || !st->A || !st->S || !st->p)
+    return HCRAN_EINVAL;
+  const InstDesc &d = h->descs[index];
+  const DLayout dl = dlayout(d.M, d.N, d.K, d.Ks, d.l);
+  const FLayout fl = flayout(d.M, d.N, d.K, d.l, nchunk_cap(d.N, d.K));
+  const ILayout il = ilayout(d.M, d.N, d.K, d.Ks, d.l);
+  const double *cst = h->dimage.data() + d.d_off;  // the instance's constants (pmax)
+  const int M = d.M, N = d.N, K = d.K, l = d.l, U = d.U;
+  const int Up = slot_stride(M, l), NPp = pair_stride(M, l), npair = d.npair;
+  // the state must be a valid allocation: A_k in [-1, M); per (n, m) at most
+  // l distinct users of m, packed at the front; powers finite in [0, mask];
+  // multipliers finite, xi' and zeta_sic' >= 0, zeta' in [1e-6, 1e6]
+  for (int k = 0; k < K; k++)
+    if (st->A[k] < -1 || st->A[k] >= M) return HCRAN_EINVAL;
+  std::vector<int32_t> Simg(size_t(N) * Up, -1);
+  std::vector<float> pimg(size_t(N) * Up, 0.f), aimg(size_t(N) * Up, 1.f), bimg(size_t(N) * Up, 0.f);
+  for (int n = 0; n < N; n++)
+    for (int m = 0; m < M; m++) {
+      const double mask = cst[dl.pmax + m] / N;
+      bool ended = false;
+      for (int s2 = 0; s2 < l; s2++) {
+        const size_t i = (size_t(n) * M + m) * l + s2, e = size_t(n) * Up + m * l + s2;
+        const int32_t k = st->S[i];
+        if (k < 0) {
+          if (k != -1) return HCRAN_EINVAL;
+          ended = true;
+          continue;
+        }
+        if (ended || k >= K || st->A[k] != m) return HCRAN_EINVAL;
+        for (int b = 0; b < s2; b++)
+          if (st->S[i - s2 + b] == k) return HCRAN_EINVAL;
+        const float pv = st->p[i];
+        if (!(pv >= 0.f) || !(pv <= mask * (1.0 + 1e-6))) return HCRAN_EINVAL;
+        Simg[e] = k;
+        pimg[e] = pv;
+        if (st->alpha) aimg[e] = st->alpha[i];
+        if (st->beta) bimg[e] = st->beta[i];
+        if (!isfinite(aimg[e]) || !isfinite(bimg[e])) return HCRAN_EINVAL;
+      }
+    }
+  (void)U;
+  std::vector<double> xi(M, 0.0), zeta(d.Ks > 0 ? d.Ks : 1, 1.0), zs(size_t(N) * NPp, 0.0);
+  for (int m = 0; m < M; m++)
+    if (st->xi) {
+      xi[m] = st->xi[m];
+      if (!(xi[m] >= 0.0) || !isfinite(xi[m])) return HCRAN_EINVAL;
+    }
+  for (int k = 0; k < d.Ks; k++)
+    if (st->zeta) {
+      zeta[k] = st->zeta[k];
+      if (!(zeta[k] >= 1e-6 && zeta[k] <= 1e6)) return HCRAN_EINVAL;
+    }
+  if (st->zeta_sic)
+    for (int n = 0; n < N; n++)
+      for (int t = 0; t < M * npair; t++) {
+        const double z = st->zeta_sic[size_t(n) * M * npair + t];
+        if (!(z >= 0.0) || !isfinite(z)) return HCRAN_EINVAL;
+        zs[size_t(n) * NPp + t] = z;
+      }
+  char *ws = static_cast<char *>(workspace_dev);
+  cudaStream_t cs = static_cast<cudaStream_t>(stream);
+  char *db = ws + h->ws.darena + sizeof(double) * d.d_off;
+  char *fb = ws + h->ws.farena + sizeof(float) * d.f_off;
+  char *ib = ws + h->ws.iarena + sizeof(int32_t) * d.i_off;
+  const cudaMemcpyKind hd = cudaMemcpyHostToDevice;
+  // pageable sources: each call returns once its source is staged
+  bool ok = cudaMemcpyAsync(ib + sizeof(int32_t) * il.A, st->A, sizeof(int32_t) * K, hd, cs) == cudaSuccess;
+  ok = ok && cudaMemcpyAsync(ib + sizeof(int32_t) * il.S, Simg.data(), sizeof(int32_t) * Simg.size(), hd, cs) ==
+                 cudaSuccess;
+  ok = ok && cudaMemcpyAsync(fb + sizeof(float) * fl.p, pimg.data(), sizeof(float) * pimg.size(), hd, cs) ==
+                 cudaSuccess;
+  ok = ok && cudaMemcpyAsync(fb + sizeof(float) * fl.alpha, aimg.data(), sizeof(float) * aimg.size(), hd, cs) ==
+                 cudaSuccess;
+  ok = ok && cudaMemcpyAsync(fb + sizeof(float) * fl.beta, bimg.data(), sizeof(float) * bimg.size(), hd, cs) ==
+                 cudaSuccess;
+  ok = ok && cudaMemcpyAsync(db + sizeof(double) * dl.xi, xi.data(), sizeof(double) * M, hd, cs) == cudaSuccess;
+  if (d.Ks > 0)
+    ok = ok && cudaMemcpyAsync(db + sizeof(double) * dl.zeta, zeta.data(), sizeof(double) * d.Ks, hd, cs) ==
+                   cudaSuccess;
+  ok = ok && cudaMemcpyAsync(db + sizeof(double) * dl.zsic, zs.data(), sizeof(double) * zs.size(), hd, cs) ==
+                 cudaSuccess;
+  if (!ok) return HCRAN_ECUDA;
+  h->descs[index].start = 1;
+  h->plan_dirty = true;
+  return HCRAN_OK;
 }
 
 extern "C" int hcran_solve_host(hcran_t h, const float *gains_host, const hcran_tol *tol,
@@ -388,6 +496,7 @@ extern "C" int hcran_solve_host(hcran_t h, const float *gains_host, const hcran_
                       st) != cudaSuccess)
     return HCRAN_ECUDA;
   rc = do_solve(h, staging, tol, workspace_dev, stream);
+  clear_start_flags(h);
   if (rc != HCRAN_OK) return rc;
   if (cudaMemcpyAsync(h->outs_host.data(), ws + h->ws.outs, sizeof(InstOut) * h->n,
                       cudaMemcpyDeviceToHost, st) != cudaSuccess ||
@@ -548,6 +657,7 @@ extern "C" int hcran_autotune(hcran_t h, const float *gains_dev, const hcran_tol
     return HCRAN_EINVAL;
   int rc = check_tol(tol);
   if (rc != HCRAN_OK) return rc;
+  if (start_pending(h)) return HCRAN_EINVAL;  // a set state applies to hcran_solve / hcran_solve_host
   char *ws = static_cast<char *>(workspace_dev);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (h->plan_dirty && upload_plan(h, ws, st) != HCRAN_OK) return HCRAN_ECUDA;
@@ -627,6 +737,7 @@ extern "C" int hcran_solve_graph(hcran_t h, const float *gains_dev, const hcran_
     return HCRAN_EINVAL;
   int rc = check_tol(tol);
   if (rc != HCRAN_OK) return rc;
+  if (start_pending(h)) return HCRAN_EINVAL;  // a set state applies to hcran_solve / hcran_solve_host
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   char *ws = static_cast<char *>(workspace_dev);
   if (h->plan_dirty && upload_plan(h, ws, st) != HCRAN_OK) return HCRAN_ECUDA;

@@ -30,6 +30,7 @@ struct Ctx {
   int M, N, K, Ks, Ke, l, U, Up, NPp, npair, nchunk;
   int crank, csize;  // rank of this CTA in the cluster that solves the instance, cluster size
   int n0, n1;        // subcarriers [n0, n1) belong to this CTA
+  int start;         // InstDesc::start
   const float *G;  // Gamma[n][m][k]
   const double *pmax, *eta, *mask, *Psi, *w;
   double *xi, *zeta, *zsic, *zsic_next;

@@ -400,6 +400,32 @@ __device__ int selection(const Ctx &c, Shared &sh, float *dyn, const KDims &kd, 
   return anych > 0;
 }
 
+// The start point written by hcran_set_state (A, S, p, alpha, beta, xi',
+// zeta', zeta_sic' in the workspace): Again, the slab and the FP32 copy of
+// zeta' derived from it, as initial_state derives them for p^0.  Sec. III
+// carries the point p^{i-1} and its multipliers into iteration i; a solve
+// that starts here continues a solve stopped after iteration i - 1.
+__device__ void resume_state(const Ctx &c, float *szeta) {
+  for (int k = cl_first(c); k < c.K; k += cl_stride(c)) {  // FP64 sums in subcarrier order
+    int best = 0;
+    double bv = -1.0;
+    for (int m = 0; m < c.M; m++) {
+      double t = 0.0;
+      for (int n = 0; n < c.N; n++) t += (double)gain(c, n, m, k);
+      if (t > bv) {
+        bv = t;
+        best = m;
+      }
+    }
+    c.Again[k] = best;
+  }
+  for (int e = c.n0 * c.Up + threadIdx.x; e < c.n1 * c.Up; e += kThreads) c.plin[e] = c.p[e];
+  for (int t = c.n0 * c.NPp + threadIdx.x; t < c.n1 * c.NPp; t += kThreads) c.zsic_next[t] = c.zsic[t];
+  for (int k = threadIdx.x; k < c.Ks; k += kThreads) szeta[k] = (float)c.zeta[k];
+  inst_sync(c);
+  build_slab(c);
+}
+
 // p^0: A_k = Again_k = argmax_m sum_n Gamma, the l strongest users of m on every
 // subcarrier (already in SIC order), p = mask / l; xi' = 0, zeta' = 1.
 __device__ void initial_state(const Ctx &c, float *szeta) {

@@ -125,7 +125,8 @@ __device__ void solve_instance(const Ctx &c, Shared &sh, float *dyn, const KDims
   __syncthreads();
   long long *cyc = sh.cyc;  // written by thread 0 only
   const long long t_begin = clock64();
-  initial_state(c, szeta);
+  if (tol.mode == kModeCold && c.start == 1) resume_state(c, szeta);
+  else initial_state(c, szeta);
   if (tol.mode == kModeFeatures) {  // initial selection and the warm-start features only
     warm_features(c);
     inst_sync(c);
@@ -148,6 +149,9 @@ __device__ void solve_instance(const Ctx &c, Shared &sh, float *dyn, const KDims
       sh.qeta[m] = (float)(q * c.eta[m]);
       sh.xif[m] = (float)c.xi[m];
     }
+    // the streaming multipliers as stored between dual loops, so that a solve
+    // resumed from an exported state takes the same steps
+    for (int k = threadIdx.x; k < c.Ks; k += kThreads) szeta[k] = (float)c.zeta[k];
     __syncthreads();
     const long long ta = clock64();
     selection(c, sh, dyn, kd, szeta, tol.tie_eps, phase, pending);
@@ -262,7 +266,7 @@ __device__ void bind(Ctx &c, const InstDesc &d, const float *gains, double *dare
                      int *iarena) {
   c.M = d.M; c.N = d.N; c.K = d.K; c.Ks = d.Ks; c.Ke = d.K - d.Ks; c.l = d.l;
   c.U = d.U; c.Up = slot_stride(d.M, d.l); c.NPp = pair_stride(d.M, d.l);
-  c.npair = d.npair; c.nchunk = d.nchunk;
+  c.npair = d.npair; c.nchunk = d.nchunk; c.start = d.start;
   c.G = gains + d.g_off;
   c.sigma = (float)d.sigma;
   c.Pconst = d.Pconst;

@@ -39,7 +39,8 @@ HCRAN_HD int pair_stride(int M, int l) {
 
 // per-instance descriptor (device copy lives at the start of the workspace)
 struct InstDesc {
-  int32_t M, N, K, Ks, l, U, L, npair, nchunk, pad;
+  int32_t M, N, K, Ks, l, U, L, npair, nchunk;
+  int32_t start;   // 0: the cold initial point p^0; 1: the state hcran_set_state wrote (next solve only)
   int64_t g_off;   // element offset of Gamma[n][m][k] in the gain buffer
   int64_t d_off;   // element offset in the double arena
   int64_t f_off;   // element offset in the float arena

@@ -60,7 +60,8 @@ EXPORTS = ["hcran_create", "hcran_workspace_size", "hcran_gain_elems", "hcran_pr
            "hcran_solve", "hcran_solve_host", "hcran_get", "hcran_get_summary",
            "hcran_get_phase_cycles", "hcran_last_launch_count", "hcran_destroy",
            "hcran_solve_noalloc", "hcran_get_schedule", "hcran_set_schedule", "hcran_autotune",
-           "hcran_solve_graph", "hcran_warm_rows", "hcran_warm_features", "hcran_solve_warm"]
+           "hcran_solve_graph", "hcran_warm_rows", "hcran_warm_features", "hcran_solve_warm",
+           "hcran_set_state"]
 # include/hcran_mlp.h: tensor-core kernels of the warm-start network
 MLP_EXPORTS = ["hcran_mlp_dense", "hcran_mlp_tc_status", "hcran_mlp_create", "hcran_mlp_destroy",
                "hcran_mlp_param_count", "hcran_mlp_get_params", "hcran_mlp_set_params", "hcran_mlp_get_grads",
@@ -99,6 +100,7 @@ def load(build_if_missing: bool = True):
         "hcran_warm_rows": ([vp, _i64p], C.c_int),
         "hcran_warm_features": ([vp, vp, vp, vp, vp], C.c_int),
         "hcran_solve_warm": ([vp, vp, C.POINTER(Tol), vp, vp, vp], C.c_int),
+        "hcran_set_state": ([vp, vp, C.c_int32, C.POINTER(Result), vp], C.c_int),
         "hcran_mlp_dense": ([vp, vp, vp, vp, C.c_int64, C.c_int32, C.c_int32, C.c_int32, vp, vp], C.c_int),
         "hcran_mlp_tc_status": ([_ip], C.c_int),
         "hcran_mlp_create": ([C.POINTER(vp), C.c_uint64, C.c_int64], C.c_int),
@@ -226,6 +228,28 @@ class Solver:
         _check("hcran_solve_warm", self.lib.hcran_solve_warm(
             self.h, C.c_void_p(gains.data_ptr()), C.byref(tol), C.c_void_p(self.workspace.data_ptr()),
             C.c_void_p(self.stream.cuda_stream), C.c_void_p(net_out.data_ptr())))
+
+    def set_state(self, i: int, state: dict):
+        """Start instance i of the next solve from `state` (a dict as get()
+        returns; A, S, p required, the multipliers optional)."""
+        inst = self.instances[i]
+        N, M, K, Ks, l = inst.N, inst.M, inst.K, inst.Ks, inst.l
+        keep = []
+
+        def arr(name, dtype, size):
+            if state.get(name) is None:
+                return None
+            a = np.ascontiguousarray(np.asarray(state[name], dtype=dtype).reshape(-1)[:size])
+            keep.append(a)
+            return a.ctypes.data_as(_ip if dtype == np.int32 else (_fp if dtype == np.float32 else _dp))
+        L, npair = N * M * l, l * (l - 1) // 2
+        r = Result()
+        r.A, r.S, r.p = arr("A", np.int32, K), arr("S", np.int32, L), arr("p", np.float32, L)
+        r.alpha, r.beta = arr("alpha", np.float32, L), arr("beta", np.float32, L)
+        r.xi, r.zeta = arr("xi", np.float64, M), arr("zeta", np.float64, Ks) if Ks else None
+        r.zeta_sic = arr("zeta_sic", np.float64, N * M * npair) if npair else None
+        _check("hcran_set_state", self.lib.hcran_set_state(
+            self.h, C.c_void_p(self.workspace.data_ptr()), int(i), C.byref(r), C.c_void_p(self.stream.cuda_stream)))
 
     def solve_host(self, gains_host, tol: Tol):
         """End-to-end solve from host gains; returns (ee, status) host arrays."""

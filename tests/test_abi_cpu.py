@@ -226,3 +226,67 @@ def test_set_schedule_accepts_every_cluster_size_that_fits():
     too_many = np.array([1, 1, 9], np.int32)  # more CTAs than the portable cluster limit
     assert lib.hcran_set_schedule(h, too_many.ctypes.data_as(hcran._ip)) == 1
     lib.hcran_destroy(h)
+
+
+def test_set_state_rejects_invalid_states_on_the_host():
+    """hcran_set_state checks the state before any copy: NULL handle, workspace
+    or arrays, an index out of range, a user on an RRH other than A_k (C5), a
+    hole before a user (packing), a repeated user, a power above the mask or
+    negative, a negative multiplier, zeta' out of range.  Each returns
+    HCRAN_EINVAL without touching a device (none is needed here)."""
+    lib = hcran.load()
+    inst = make_workload("small-3x8x6")[0]
+    c, keep = _cfg(inst)
+    arr = (hcran.Config * 1)(c)
+    h = C.c_void_p()
+    assert lib.hcran_create(C.byref(h), arr, 1, None) == 0
+    N, M, K, Ks, l = inst.N, inst.M, inst.K, inst.Ks, inst.l
+    mask = inst.pmax / N
+
+    def state(**over):
+        A = np.array([0, 0, 1, 2, 0, 1], np.int32)
+        S = -np.ones((N, M, l), np.int32)
+        p = np.zeros((N, M, l), np.float32)
+        for n in range(N):
+            S[n, 0, :2] = [0, 1]
+            S[n, 1, 0] = 2
+            p[n, 0, :2] = mask[0] / 4
+            p[n, 1, 0] = mask[1] / 2
+        d = dict(A=A, S=S, p=p, xi=np.zeros(M), zeta=np.ones(Ks), zeta_sic=np.zeros(N * M))
+        d.update(over)
+        return d
+
+    def call(st, ws=256, index=0):
+        ks = []
+
+        def a(x, t, tp):
+            if x is None:
+                return None
+            y = np.ascontiguousarray(x, dtype=t).reshape(-1)
+            ks.append(y)
+            return y.ctypes.data_as(tp)
+        r = hcran.Result()
+        r.A, r.S, r.p = a(st["A"], np.int32, hcran._ip), a(st["S"], np.int32, hcran._ip), a(st["p"], np.float32, hcran._fp)
+        r.xi, r.zeta = a(st.get("xi"), np.float64, hcran._dp), a(st.get("zeta"), np.float64, hcran._dp)
+        r.zeta_sic = a(st.get("zeta_sic"), np.float64, hcran._dp)
+        return lib.hcran_set_state(h, C.c_void_p(ws), index, C.byref(r), None)
+
+    assert lib.hcran_set_state(None, C.c_void_p(256), 0, None, None) == 1
+    assert call(state(), ws=0) == 1              # no workspace
+    assert call(state(), ws=300) == 1            # misaligned workspace
+    assert call(state(), index=1) == 1           # index out of range
+    assert call(state(A=None)) == 1              # A required
+    bad = []
+    s = state(); s["S"][0, 1, 0] = 0; bad.append(s)            # user 0 on RRH 1 but A_0 = 0 (C5)
+    s = state(); s["S"][0, 0, 0] = -1; bad.append(s)           # a hole before a user
+    s = state(); s["S"][0, 0, 1] = 0; bad.append(s)            # user 0 twice on (0, 0)
+    s = state(); s["S"][0, 0, 0] = 7; bad.append(s)            # no such user
+    s = state(); s["A"][3] = 3; bad.append(s)                  # no such RRH
+    s = state(); s["p"][0, 0, 0] = mask[0] * 1.01; bad.append(s)   # above the mask (C4)
+    s = state(); s["p"][0, 0, 0] = -1e-6; bad.append(s)        # negative power
+    s = state(); s["xi"] = -np.ones(M); bad.append(s)          # negative multiplier
+    s = state(); s["zeta"] = np.full(Ks, 1e7); bad.append(s)   # zeta' above 1e6
+    s = state(); s["zeta_sic"] = np.full(N * M, np.nan); bad.append(s)
+    for i, s in enumerate(bad):
+        assert call(s) == 1, i
+    lib.hcran_destroy(h)

@@ -38,6 +38,7 @@ static int null_calls(void) {
   bad += hcran_warm_features(NULL, NULL, NULL, NULL, NULL) != HCRAN_EINVAL;
   bad += hcran_solve_warm(NULL, NULL, NULL, NULL, NULL, NULL) != HCRAN_EINVAL;
   bad += hcran_solve_noalloc(NULL, NULL, NULL, NULL, NULL) != HCRAN_EINVAL;
+  bad += hcran_set_state(NULL, NULL, 0, NULL, NULL) != HCRAN_EINVAL;
   hcran_destroy(NULL);
   bad += hcran_mlp_dense(NULL, NULL, NULL, NULL, 0, 16, 16, 0, NULL, NULL) != HCRAN_MLP_EINVAL;
   bad += hcran_mlp_tc_status(NULL) != HCRAN_MLP_EINVAL;
