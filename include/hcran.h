@@ -41,8 +41,8 @@ typedef enum {
   HCRAN_EINVAL = 1,    /* bad argument (sizes, NULL, NaN/negative constants, misaligned offset) */
   HCRAN_ENOMEM = 2,    /* host allocation failed or workspace too small */
   HCRAN_ECUDA = 3,     /* a CUDA runtime call failed (launch, copy, sync) */
-  HCRAN_ETIMEDOUT = 4, /* reserved: a bounded device wait gave up */
-  HCRAN_ENUMERIC = 5,  /* NaN/Inf reached the Dinkelbach ratio */
+  HCRAN_ETIMEDOUT = 4, /* a bounded device wait gave up (hcran_get, hcran_solve_host) */
+  HCRAN_ENUMERIC = 5,  /* a non-finite or negative gain, or NaN/Inf in the Dinkelbach ratio */
   HCRAN_E2BIG = 6      /* the instance does not fit the fixed scratch of hcran_solve_noalloc */
 } hcran_status;
 
@@ -50,7 +50,7 @@ typedef enum {
 #define HCRAN_ST_NOT_CONVERGED 1   /* Dinkelbach cap reached before F(q) <= tol * R */
 #define HCRAN_ST_STREAMING_UNMET 2 /* some streaming user ends below Psi_k (relative slack < -1e-3) */
 #define HCRAN_ST_EE_DECREASED 4    /* the output's EE is below an earlier Dinkelbach iterate's (kept for C13) */
-#define HCRAN_ST_NUMERIC 8         /* non-finite value met; the instance's outputs are not valid */
+#define HCRAN_ST_NUMERIC 8         /* non-finite or negative gain, or non-finite R/P; outputs not valid */
 #define HCRAN_ST_TIMEOUT 16        /* a bounded wait for a shared-memory copy gave up; outputs not valid */
 
 typedef struct hcran_s *hcran_t;
@@ -139,10 +139,25 @@ int hcran_solve(hcran_t h, const float *gains_dev, const hcran_tol *tol, void *w
 int hcran_solve_host(hcran_t h, const float *gains_host, const hcran_tol *tol, void *workspace_dev,
                      void *stream, double *ee_host, int32_t *status_host);
 
-/* Results.  Both synchronise the stream of the last solve. */
+/* Results.  Both synchronise the stream of the last solve.  hcran_get fills
+ * `out` and returns HCRAN_ETIMEDOUT when the instance's status carries
+ * HCRAN_ST_TIMEOUT, HCRAN_ENUMERIC when it carries HCRAN_ST_NUMERIC (the
+ * other instances of the batch are unaffected); hcran_solve_host returns the
+ * same codes when any instance carries them. */
 int hcran_get(hcran_t h, int32_t index, hcran_result *out);
 int hcran_get_summary(hcran_t h, double *ee, double *R, double *P, int32_t *status,
                       int32_t *iters3, double *min_margin, int32_t *n_ties);
+
+/* Bound of every device wait, and a test of the path that reports a wait
+ * that gave up.  The solver's waits on shared-memory copies (mbarrier
+ * try-waits) give up after max_tries tries (0 = the default, 2^22), and the
+ * instance then ends with HCRAN_ST_TIMEOUT.  stall_instance >= 0 makes the
+ * solve of that instance first wait on a barrier that nothing completes (no
+ * copy in flight), so that this wait gives up and the instance reports the
+ * timeout while the others solve normally; -1 turns it off.  Applies to the
+ * following solves of h.  HCRAN_EINVAL for max_tries < 0 or an index out of
+ * range. */
+int hcran_set_wait_limit(hcran_t h, int64_t max_tries, int32_t stall_instance);
 
 /* Start point of instance `index` for the next hcran_solve / hcran_solve_host
  * (Sec. III: iteration i of the Dinkelbach method starts from p^{i-1} and its

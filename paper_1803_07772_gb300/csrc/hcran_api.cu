@@ -45,6 +45,8 @@ struct hcran_s {
   int32_t last_launches = 0;
   std::vector<InstOut> outs_host;
   bool plan_dirty = false;  // descriptors / order changed since they were uploaded
+  int64_t spin_limit = 0;        // tries of a bounded device wait (0: the default)
+  int32_t stall_instance = -1;   // test of the failure path (hcran_set_wait_limit)
   // captured launch sequence of hcran_solve_graph and the arguments it was captured for
   cudaGraphExec_t graph = nullptr;
   const void *graph_gains = nullptr, *graph_ws = nullptr;
@@ -269,6 +271,8 @@ extern "C" int hcran_gain_elems(hcran_t h, int64_t *elems) {
   return HCRAN_OK;
 }
 
+constexpr int32_t kStatusNumericHost = HCRAN_ST_NUMERIC, kStatusTimeoutHost = HCRAN_ST_TIMEOUT;
+
 static bool ws_ok(void *ws) { return ws && (reinterpret_cast<uintptr_t>(ws) & 255) == 0; }
 
 // descriptors and launch order -> workspace (stream-ordered)
@@ -312,6 +316,8 @@ static Tol to_tol(const hcran_tol *tol) {
   t.tie_eps = (float)tol->tie_eps;
   t.q_init = tol->q_init;
   t.mode = kModeCold;
+  t.spin_limit = 0;
+  t.stall_instance = -1;
   return t;
 }
 
@@ -333,6 +339,8 @@ static int do_solve(hcran_t h, const float *gains_dev, const hcran_tol *tol, voi
   if (h->plan_dirty && upload_plan(h, ws, static_cast<cudaStream_t>(stream)) != HCRAN_OK) return HCRAN_ECUDA;
   Tol t = to_tol(tol);
   t.mode = mode;
+  t.spin_limit = h->spin_limit;
+  t.stall_instance = h->stall_instance;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (!h->side) {
     if (cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess ||
@@ -392,6 +400,17 @@ extern "C" int hcran_solve(hcran_t h, const float *gains_dev, const hcran_tol *t
   const int r = do_solve(h, gains_dev, tol, workspace_dev, stream);
   clear_start_flags(h);
   return r;
+}
+
+extern "C" int hcran_set_wait_limit(hcran_t h, int64_t max_tries, int32_t stall_instance) {
+  if (!h || max_tries < 0 || stall_instance < -1 || stall_instance >= h->n) return HCRAN_EINVAL;
+  h->spin_limit = max_tries;
+  h->stall_instance = stall_instance;
+  if (h->graph) {  // the captured launches carry the old settings
+    cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+  }
+  return HCRAN_OK;
 }
 
 extern "C" int hcran_set_state(hcran_t h, void *workspace_dev, int32_t index, const hcran_result *st,
@@ -502,11 +521,14 @@ extern "C" int hcran_solve_host(hcran_t h, const float *gains_host, const hcran_
                       cudaMemcpyDeviceToHost, st) != cudaSuccess ||
       cudaStreamSynchronize(st) != cudaSuccess)
     return HCRAN_ECUDA;
+  int worst = HCRAN_OK;
   for (int32_t b = 0; b < h->n; b++) {
     if (ee_host) ee_host[b] = h->outs_host[b].ee;
     if (status_host) status_host[b] = h->outs_host[b].status;
+    if (h->outs_host[b].status & kStatusTimeoutHost) worst = HCRAN_ETIMEDOUT;
+    else if ((h->outs_host[b].status & kStatusNumericHost) && worst == HCRAN_OK) worst = HCRAN_ENUMERIC;
   }
-  return HCRAN_OK;
+  return worst;
 }
 
 static int sync_last(hcran_t h) {
@@ -561,6 +583,8 @@ extern "C" int hcran_get(hcran_t h, int32_t index, hcran_result *out) {
   out->slack_sic_max = o.slack_sic_max;
   out->min_margin = o.min_margin;
   out->n_ties = o.n_ties;
+  if (o.status & kStatusTimeoutHost) return HCRAN_ETIMEDOUT;
+  if (o.status & kStatusNumericHost) return HCRAN_ENUMERIC;
   return HCRAN_OK;
 }
 

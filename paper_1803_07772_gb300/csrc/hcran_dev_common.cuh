@@ -19,7 +19,7 @@ constexpr float kInvLn2 = 1.44269504f;
 constexpr double kZetaAsumMin = 0.05;
 constexpr double kZetaMin = 1e-6, kZetaMax = 1e6;
 constexpr float kLog2ZetaMin = -19.9315686f, kLog2ZetaMax = 19.9315686f;  // log2 of the bounds
-constexpr int kSpinLimit = 1 << 22;  // bound on every mbarrier wait
+constexpr int kSpinLimit = 1 << 22;  // default bound on every mbarrier wait (tries)
 constexpr int kStatusTimeout = 16;   // per-instance status bit: a bounded wait gave up
 
 // dynamic shared memory of the solver kernel (one declaration for every
@@ -70,6 +70,8 @@ struct Shared {
   double vpart[kMaxM], vtot[kMaxM];  // per-RRH vectors summed over the cluster
   int inst;
   int abort;
+  long long spin_limit;          // tries of a bounded mbarrier wait (Tol::spin_limit or the default)
+  unsigned long long stall_bar;  // initialised once, never arrived at: a wait on it can only give up
   float min_margin;
   int n_ties;
 };
@@ -200,8 +202,8 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, uint32_t 
   return ok != 0;
 }
 // bounded wait; returns false when the limit was reached
-__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, uint32_t parity) {
-  for (int i = 0; i < kSpinLimit; i++)
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, uint32_t parity, long long limit) {
+  for (long long i = 0; i < limit; i++)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
 }

@@ -64,7 +64,7 @@ __device__ float sweep(const Ctx &c, Shared &sh, float *dyn, const KDims &kd, co
         if (lane == 0) issue_stage(c, sh, kd, b ? wb.stage0 : wb.stage1, warp, b ^ 1, nn, zsrc);
         pending |= 2u >> b;  // bit of buffer b^1
       }
-      const bool ok = mbar_wait(&sh.bar[warp][b], (phase >> b) & 1u);
+      const bool ok = mbar_wait(&sh.bar[warp][b], (phase >> b) & 1u, sh.spin_limit);
       phase ^= 1u << b;
       pending &= ~(1u << b);
       if (!ok) sh.abort = 1;

@@ -405,13 +405,19 @@ __device__ int selection(const Ctx &c, Shared &sh, float *dyn, const KDims &kd, 
 // zeta' derived from it, as initial_state derives them for p^0.  Sec. III
 // carries the point p^{i-1} and its multipliers into iteration i; a solve
 // that starts here continues a solve stopped after iteration i - 1.
-__device__ void resume_state(const Ctx &c, float *szeta) {
+// Returns the number of non-finite or negative gains this thread read.
+__device__ int resume_state(const Ctx &c, float *szeta) {
+  int bad = 0;
   for (int k = cl_first(c); k < c.K; k += cl_stride(c)) {  // FP64 sums in subcarrier order
     int best = 0;
     double bv = -1.0;
     for (int m = 0; m < c.M; m++) {
       double t = 0.0;
-      for (int n = 0; n < c.N; n++) t += (double)gain(c, n, m, k);
+      for (int n = 0; n < c.N; n++) {
+        const float g = gain(c, n, m, k);
+        bad += !(g >= 0.f && g < INFINITY);
+        t += (double)g;
+      }
       if (t > bv) {
         bv = t;
         best = m;
@@ -424,12 +430,15 @@ __device__ void resume_state(const Ctx &c, float *szeta) {
   for (int k = threadIdx.x; k < c.Ks; k += kThreads) szeta[k] = (float)c.zeta[k];
   inst_sync(c);
   build_slab(c);
+  return bad;
 }
 
 // p^0: A_k = Again_k = argmax_m sum_n Gamma, the l strongest users of m on every
 // subcarrier (already in SIC order), p = mask / l; xi' = 0, zeta' = 1.
-__device__ void initial_state(const Ctx &c, float *szeta) {
+// Returns the number of non-finite or negative gains this thread read.
+__device__ int initial_state(const Ctx &c, float *szeta) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int bad = 0;
   for (int e = c.n0 * c.Up + threadIdx.x; e < c.n1 * c.Up; e += kThreads) {
     c.S[e] = -1;
     c.p[e] = 0.f;
@@ -442,7 +451,11 @@ __device__ void initial_state(const Ctx &c, float *szeta) {
     double bv = -1.0;
     for (int m = 0; m < c.M; m++) {
       double t = 0.0;
-      for (int n = 0; n < c.N; n++) t += (double)gain(c, n, m, k);
+      for (int n = 0; n < c.N; n++) {
+        const float g = gain(c, n, m, k);
+        bad += !(g >= 0.f && g < INFINITY);
+        t += (double)g;
+      }
       if (t > bv) {
         bv = t;
         best = m;
@@ -499,6 +512,7 @@ __device__ void initial_state(const Ctx &c, float *szeta) {
   }
   __syncthreads();
   build_slab(c);
+  return bad;
 }
 
 }  // namespace hcran

@@ -86,7 +86,7 @@ __device__ void restore_iterate(const Ctx &c, float *szeta) {
 }
 
 __device__ void solve_instance(const Ctx &c, Shared &sh, float *dyn, const KDims &kd, const Tol &tol,
-                               InstOut *out, unsigned &phase, unsigned &pending) {
+                               InstOut *out, int index, unsigned &phase, unsigned &pending) {
   float *szeta = dyn;  // streaming multipliers in FP32, first in dynamic shared memory
   for (int m = threadIdx.x; m < c.M; m += kThreads) {
     sh.maskf[m] = (float)c.mask[m];
@@ -123,10 +123,18 @@ __device__ void solve_instance(const Ctx &c, Shared &sh, float *dyn, const KDims
     sh.abort = 0;
   }
   __syncthreads();
+  // test of the failure path (Tol::stall_instance): a bounded wait on a
+  // barrier that nothing completes, with no copy in flight, gives up after
+  // spin_limit tries; every CTA of the cluster waits and gives up alike, so
+  // they skip the solve together and report HCRAN_ST_TIMEOUT
+  if (index == tol.stall_instance && threadIdx.x == 0 && !mbar_wait(&sh.stall_bar, 0u, sh.spin_limit))
+    sh.abort = 1;
   long long *cyc = sh.cyc;  // written by thread 0 only
   const long long t_begin = clock64();
-  if (tol.mode == kModeCold && c.start == 1) resume_state(c, szeta);
-  else initial_state(c, szeta);
+  // the set-up reads every gain once: a non-finite or negative one makes the
+  // instance's results invalid (HCRAN_ST_NUMERIC), decided by the whole cluster
+  const int bad_gains = cl_isum(tol.mode == kModeCold && c.start == 1 ? resume_state(c, szeta)
+                                                                       : initial_state(c, szeta), sh, c);
   if (tol.mode == kModeFeatures) {  // initial selection and the warm-start features only
     warm_features(c);
     inst_sync(c);
@@ -137,12 +145,12 @@ __device__ void solve_instance(const Ctx &c, Shared &sh, float *dyn, const KDims
   link_all<kLinkOnly>(c, sh, dyn, kd, szeta, 0.f, phase, pending);
   exact_R_P(c, sh, R, P);
   double q = tol.q_init > 0.0 ? tol.q_init : R / P;
-  int it_d = 0, it_s = 0, it_v = 0, status = 1;  // not converged until the stop test fires
+  int it_d = 0, it_s = 0, it_v = 0, status = bad_gains ? 8 : 1;  // not converged until the stop test fires
   const int Imax = tol.max_dinkelbach > 0 ? tol.max_dinkelbach : 1;
   const int Smax = tol.max_scale > 0 ? tol.max_scale : 1;
   float slack_prev = rate_slack_min(c, sh);
   double ee_best = R / P;
-  for (int i = 0; i < Imax && !sh.abort; i++) {
+  for (int i = 0; i < Imax && !sh.abort && !bad_gains; i++) {
     save_iterate(c);  // p^{i-1}, kept if Algorithm 1 ends below it
     const double q_prev = q;
     for (int m = threadIdx.x; m < c.M; m += kThreads) {
@@ -314,6 +322,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     mbar_init(&sh.bar[warp][0], 1);
     mbar_init(&sh.bar[warp][1], 1);
   }
+  if (threadIdx.x == 0) {
+    mbar_init(&sh.stall_bar, 1);
+    sh.spin_limit = tol.spin_limit > 0 ? tol.spin_limit : (long long)kSpinLimit;
+  }
   fence_mbar_init();
   __syncthreads();
   unsigned phase = 0, pending = 0;  // per-warp mbarrier parity and copies in flight
@@ -340,12 +352,12 @@ __global__ void __launch_bounds__(kThreads, 1)
       sc.n1 = (int)((int64_t)sc.N * (crank + 1) / csize);
     }
     __syncthreads();
-    solve_instance(sc, sh, dyn, kd, tol, outs + b, phase, pending);
+    solve_instance(sc, sh, dyn, kd, tol, outs + b, b, phase, pending);
   }
   // never leave a bulk copy in flight (bounded; set only after a timed-out wait)
   for (int bb = 0; bb < 2; bb++)
     if (pending & (1u << bb)) {
-      mbar_wait(&sh.bar[warp][bb], (phase >> bb) & 1u);
+      mbar_wait(&sh.bar[warp][bb], (phase >> bb) & 1u, sh.spin_limit);
     }
 }
 

@@ -330,6 +330,8 @@ struct Tol {
   float tie_eps;
   double q_init;
   int32_t mode;  // SolveMode
+  int64_t spin_limit;      // tries of every bounded mbarrier wait (<= 0: the default)
+  int32_t stall_instance;  // instance whose solve first waits on a barrier nothing completes (-1: none)
 };
 
 // warm-start rows (one per slot: row s_off + n * Up + u): the features the

@@ -196,6 +196,8 @@ extern "C" int hcran_solve_noalloc(const hcran_config *cfg, const float *gains_d
   t.tie_eps = (float)tol->tie_eps;
   t.q_init = tol->q_init;
   t.mode = kModeCold;
+  t.spin_limit = 0;
+  t.stall_instance = -1;
   int launches = 0;
   if (launch_solve(reinterpret_cast<const InstDesc *>(ws + p.o_desc),
                    reinterpret_cast<const int *>(ws + p.o_order), 1, gains_dev, db,

@@ -61,7 +61,7 @@ EXPORTS = ["hcran_create", "hcran_workspace_size", "hcran_gain_elems", "hcran_pr
            "hcran_get_phase_cycles", "hcran_last_launch_count", "hcran_destroy",
            "hcran_solve_noalloc", "hcran_get_schedule", "hcran_set_schedule", "hcran_autotune",
            "hcran_solve_graph", "hcran_warm_rows", "hcran_warm_features", "hcran_solve_warm",
-           "hcran_set_state"]
+           "hcran_set_state", "hcran_set_wait_limit"]
 # include/hcran_mlp.h: tensor-core kernels of the warm-start network
 MLP_EXPORTS = ["hcran_mlp_dense", "hcran_mlp_tc_status", "hcran_mlp_create", "hcran_mlp_destroy",
                "hcran_mlp_param_count", "hcran_mlp_get_params", "hcran_mlp_set_params", "hcran_mlp_get_grads",
@@ -101,6 +101,7 @@ def load(build_if_missing: bool = True):
         "hcran_warm_features": ([vp, vp, vp, vp, vp], C.c_int),
         "hcran_solve_warm": ([vp, vp, C.POINTER(Tol), vp, vp, vp], C.c_int),
         "hcran_set_state": ([vp, vp, C.c_int32, C.POINTER(Result), vp], C.c_int),
+        "hcran_set_wait_limit": ([vp, C.c_int64, C.c_int32], C.c_int),
         "hcran_mlp_dense": ([vp, vp, vp, vp, C.c_int64, C.c_int32, C.c_int32, C.c_int32, vp, vp], C.c_int),
         "hcran_mlp_tc_status": ([_ip], C.c_int),
         "hcran_mlp_create": ([C.POINTER(vp), C.c_uint64, C.c_int64], C.c_int),
@@ -257,9 +258,11 @@ class Solver:
         ee = np.zeros(n)
         st = np.zeros(n, np.int32)
         ptr = gains_host.data_ptr() if hasattr(gains_host, "data_ptr") else gains_host.ctypes.data
-        _check("hcran_solve_host", self.lib.hcran_solve_host(
+        rc = self.lib.hcran_solve_host(
             self.h, C.c_void_p(ptr), C.byref(tol), C.c_void_p(self.workspace.data_ptr()),
-            C.c_void_p(self.stream.cuda_stream), ee.ctypes.data_as(_dp), st.ctypes.data_as(_ip)))
+            C.c_void_p(self.stream.cuda_stream), ee.ctypes.data_as(_dp), st.ctypes.data_as(_ip))
+        if rc not in (0, 4, 5):  # ETIMEDOUT / ENUMERIC: per-instance status bits in st
+            _check("hcran_solve_host", rc)
         return ee, st
 
     def launches(self) -> int:
@@ -285,14 +288,20 @@ class Solver:
         for k, a in arr.items():
             t = _ip if a.dtype == np.int32 else (_fp if a.dtype == np.float32 else _dp)
             setattr(r, k, a.ctypes.data_as(t))
-        _check("hcran_get", self.lib.hcran_get(self.h, i, C.byref(r)))
+        rc = self.lib.hcran_get(self.h, i, C.byref(r))
+        if rc not in (0, 4, 5):  # ETIMEDOUT / ENUMERIC: the status bits say which; outputs are filled
+            _check("hcran_get", rc)
         return dict(A=arr["A"], S=arr["S"].reshape(N, M, l), p=arr["p"].reshape(N, M, l),
                     alpha=arr["alpha"].reshape(N, M, l), beta=arr["beta"].reshape(N, M, l),
                     xi=arr["xi"], zeta=arr["zeta"][:Ks],
                     zeta_sic=arr["zeta_sic"][:N * M * npair].reshape(N, M, npair),
                     ee=r.ee, R=r.R, P=r.P, iters=tuple(r.iters), status=r.status,
                     slack_power_min=r.slack_power_min, slack_rate_min=r.slack_rate_min,
-                    slack_sic_max=r.slack_sic_max, min_margin=r.min_margin, n_ties=r.n_ties)
+                    slack_sic_max=r.slack_sic_max, min_margin=r.min_margin, n_ties=r.n_ties, rc=rc)
+
+    def set_wait_limit(self, max_tries: int = 0, stall_instance: int = -1):
+        """Bound of the device waits; stall_instance >= 0 tests the timeout path on that instance."""
+        _check("hcran_set_wait_limit", self.lib.hcran_set_wait_limit(self.h, int(max_tries), int(stall_instance)))
 
     def phase_cycles(self) -> np.ndarray:
         """[n, 8] SM cycles per phase of the last solve (see include/hcran.h)."""

@@ -290,3 +290,19 @@ def test_set_state_rejects_invalid_states_on_the_host():
     for i, s in enumerate(bad):
         assert call(s) == 1, i
     lib.hcran_destroy(h)
+
+
+def test_set_wait_limit_validates_its_arguments():
+    lib = hcran.load()
+    inst = make_workload("small-3x8x6")[0]
+    c, keep = _cfg(inst)
+    arr = (hcran.Config * 1)(c)
+    h = C.c_void_p()
+    assert lib.hcran_create(C.byref(h), arr, 1, None) == 0
+    assert lib.hcran_set_wait_limit(h, 0, -1) == 0
+    assert lib.hcran_set_wait_limit(h, 1000, 0) == 0
+    assert lib.hcran_set_wait_limit(h, -1, -1) == 1      # negative bound
+    assert lib.hcran_set_wait_limit(h, 0, 1) == 1        # no instance 1
+    assert lib.hcran_set_wait_limit(h, 0, -2) == 1
+    assert lib.hcran_set_wait_limit(None, 0, -1) == 1
+    lib.hcran_destroy(h)

@@ -39,6 +39,7 @@ static int null_calls(void) {
   bad += hcran_solve_warm(NULL, NULL, NULL, NULL, NULL, NULL) != HCRAN_EINVAL;
   bad += hcran_solve_noalloc(NULL, NULL, NULL, NULL, NULL) != HCRAN_EINVAL;
   bad += hcran_set_state(NULL, NULL, 0, NULL, NULL) != HCRAN_EINVAL;
+  bad += hcran_set_wait_limit(NULL, 0, -1) != HCRAN_EINVAL;
   hcran_destroy(NULL);
   bad += hcran_mlp_dense(NULL, NULL, NULL, NULL, 0, 16, 16, 0, NULL, NULL) != HCRAN_MLP_EINVAL;
   bad += hcran_mlp_tc_status(NULL) != HCRAN_MLP_EINVAL;
