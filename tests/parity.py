@@ -7,7 +7,7 @@ Test infrastructure only.  An instance meets the bar in one of four ways:
     Against the plain oracle: the RRH choice A_k equal for every served user;
     on every (n, m) the same users, apart from vanishing links (present on one
     side only and carrying less than ``VANISH`` of the RRH's mask, so they
-    move neither R nor P beyond rounding); EE within ``EE_RTOL``; every power
+    move neither R nor P beyond rounding); the same status bits; EE within ``EE_RTOL``; every power
     of a link both sides select within ``P_RTOL`` relative, plus an absolute
     allowance for powers far below the mask: 1e-6 of the mask when both
     sides run the same iteration counts, else the dual loop's own stopping
@@ -133,7 +133,9 @@ def check(inst, g, o, label="", p_abs=1e-6):
     rep = dict(label=label, ee_gpu=g["ee"], ee_orc=o.ee, ee_rel=ee_err, p_maxrel=p_err, p_excess=p_excess,
                same_selection=same, sel=sel, margin_gpu=g["min_margin"], margin_orc=o.min_margin,
                status=(g["status"], o.status), iters_gpu=tuple(g["iters"]), iters_orc=tuple(o.iters))
-    rep["ok"] = bool(same and ee_err <= EE_RTOL and p_excess <= 1.0)
+    # the status bits (Dinkelbach cap, streaming rate unmet, EE below an
+    # earlier iterate) are part of the result
+    rep["ok"] = bool(same and ee_err <= EE_RTOL and p_excess <= 1.0 and (g["status"] & 7) == (o.status & 7))
     return rep
 
 
