@@ -103,3 +103,42 @@ def test_trained_warm_start_gives_valid_solves():
         print("cold ee %.4f iters %s | warm ee %.4f iters %s" % (c["ee"], c["iters"], w["ee"], w["iters"]))
         assert np.isfinite(w["ee"]) and w["ee"] >= 0.0
         assert w["slack_power_min"] >= -1e-5
+
+
+def test_warm_start_gain_against_the_exact_state_ceiling():
+    """What the trained network gains over the cold solve under the acceptance
+    rule (a warm result counts when its EE is within 1e-4 of the cold one,
+    otherwise the instance is solved cold again), measured in dual iterations,
+    the solver's unit of work; and the ceiling of any warm start: every
+    instance resumed from the cold solve's own converged state."""
+    from paper_1803_07772_gb300 import make_tol
+    from paper_1803_07772_gb300.mlp import MLP
+    from paper_1803_07772_gb300.warmstart import TRAIN_SEED_BASE, build_dataset, train, warm_solve
+    tol = make_tol(WORKLOADS["batch-4096-uneven"]["tol"])
+    train_insts = make_workload("batch-4096-uneven", count=48, start=TRAIN_SEED_BASE - 300000)
+    s, g = _solver(train_insts)
+    X, Y, Mk = build_dataset(s, g, train_insts, tol)
+    net = MLP(seed=5, max_rows=8192)
+    train(net, X, Y, Mk, epochs=6, batch=4096, lr=2e-3)
+    ev = _subset(16)
+    se, ge = _solver(ev)
+    se.solve(ge, tol)
+    cold = [se.get(i) for i in range(len(ev))]
+    warm_solve(se, net, ge, tol)
+    warm = [se.get(i) for i in range(len(ev))]
+    for i, c in enumerate(cold):
+        se.set_state(i, c)
+    se.solve(ge, tol)
+    exact = [se.get(i) for i in range(len(ev))]
+
+    def gain(res):
+        work_cold = sum(c["iters"][2] for c in cold)
+        acc = [abs(r["ee"] - c["ee"]) <= 1e-4 * c["ee"] for r, c in zip(res, cold)]
+        work = sum(r["iters"][2] for r in res) + sum(c["iters"][2] for c, a in zip(cold, acc) if not a)
+        return work_cold / work, float(np.mean(acc))
+    g_net, a_net = gain(warm)
+    g_ex, a_ex = gain(exact)
+    print("network: gain %.3f, accepted %.2f | exact state: gain %.3f, accepted %.2f" % (g_net, a_net, g_ex, a_ex))
+    assert a_ex >= 0.9                      # the converged state is (nearly) a fixed point of the solve
+    assert g_ex > 1.5                       # and resuming from it saves most of the work
+    assert 0.0 < g_net <= g_ex * 1.05       # no predicted start does better than the exact one
