@@ -7,6 +7,7 @@ in ``paper_1803_07772_gb300``; the two meet only at the seeded inputs drawn by
 """
 from .oracle import (  # noqa: F401
     OracleResult,
+    bruteforce,
     build,
     psi,
     scale_coeffs,

@@ -928,3 +928,191 @@ done:
   free(I.mask); free(I.pfloor); free(I.Psi); free(I.w);
   return rc;
 }
+
+/* ------------------------------------------------------------------ */
+/* global-optimum comparator: brute force over assignments              */
+/* ------------------------------------------------------------------ */
+/*
+ * Stands in for the paper's monotonic-optimisation optimum (Sec. IV-B) on
+ * small instances with elastic users only.  Every RRH choice A_k in
+ * {-1, .., M-1} and, on every (n, m), every subset of the users of m of at
+ * most l members (every user with A_k >= 0 on at least one link) is an
+ * assignment.  Enumeration order: A as a number in base M+1 (user 0 the
+ * fastest digit, digit d meaning A_k = d - 1), then the subsets of (n, m) in
+ * (n, m) order, n slowest, each (n, m) a digit over its subsets listed by size
+ * then lexicographically (user ids ascending).  For each assignment the EE
+ * (R over every link / P of the Sec. II-A power model) is maximised over the
+ * powers by coordinate golden-section search in [1e-6 mask, mask] from three
+ * starts p = f mask, f = 0.1, 0.4, 1: BF_SWEEPS sweeps over the links in
+ * assignment order, BF_GOLDEN golden-section steps per link (the upper point
+ * moves when the lower is at least as good), the midpoint kept when it
+ * improves.  A point that breaks C12 (sum over m's links > pmax_m) or C14
+ * (Omega_bar > 0 for a pair of the same (m, n) in SIC order) has value -1.
+ */
+#define BF_SWEEPS 8
+#define BF_GOLDEN 40
+#define BF_MAXL 16
+
+typedef struct {
+  int n, m, k;
+} bf_link;
+
+typedef struct {
+  const inst_t *I;
+  const bf_link *L;
+  int nl;
+} bf_ctx;
+
+static double bf_value(const bf_ctx *c, const double *p) {
+  const inst_t *I = c->I;
+  double tot[64];
+  for (int m = 0; m < I->M; m++) tot[m] = 0.0;
+  for (int j = 0; j < c->nl; j++) tot[c->L[j].m] += p[j];
+  for (int m = 0; m < I->M; m++)
+    if (tot[m] > I->pmax[m] * (1.0 + 1e-12)) return -1.0;
+  double R = 0.0, P = I->Pconst;
+  for (int j = 0; j < c->nl; j++) {
+    const bf_link a = c->L[j];
+    double intra = 0.0, inter = 0.0;
+    for (int i = 0; i < c->nl; i++) {
+      const bf_link b = c->L[i];
+      if (b.n != a.n) continue;
+      if (b.m == a.m) {
+        if (i != j && stronger(I, a.n, a.m, b.k, a.k)) intra += p[i];
+        /* C14 for the pair (stronger a, weaker b) */
+        if (i != j && stronger(I, a.n, a.m, a.k, b.k)) {
+          double xa = 0.0, xb = 0.0;
+          for (int q = 0; q < c->nl; q++) {
+            const bf_link t = c->L[q];
+            if (t.n != a.n || t.m == a.m) continue;
+            xa += gain(I, a.n, t.m, a.k) * p[q];
+            xb += gain(I, a.n, t.m, b.k) * p[q];
+          }
+          if ((I->sigma + xa) / gain(I, a.n, a.m, a.k) - (I->sigma + xb) / gain(I, a.n, a.m, b.k) > 0.0)
+            return -1.0;
+        }
+      } else {
+        inter += gain(I, a.n, b.m, a.k) * p[i];
+      }
+    }
+    const double g = gain(I, a.n, a.m, a.k);
+    R += I->w[(size_t)a.m * I->K + a.k] * log2(1.0 + p[j] * g / (I->sigma + g * intra + inter));
+    P += I->eta[a.m] * p[j];
+  }
+  return R / P;
+}
+
+static double bf_search(const bf_ctx *c) {
+  const inst_t *I = c->I;
+  const double gr = (sqrt(5.0) - 1.0) / 2.0;
+  const double starts[3] = {0.1, 0.4, 1.0};
+  double best = -1.0, p[BF_MAXL], q[BF_MAXL];
+  for (int st = 0; st < 3; st++) {
+    for (int j = 0; j < c->nl; j++) p[j] = starts[st] * I->mask[c->L[j].m];
+    double cur = bf_value(c, p);
+    if (cur < 0.0) continue;
+    for (int sw = 0; sw < BF_SWEEPS; sw++)
+      for (int j = 0; j < c->nl; j++) {
+        const double mk = I->mask[c->L[j].m];
+        double lo = 1e-6 * mk, hi = mk;
+        for (int i = 0; i < c->nl; i++) q[i] = p[i];
+        for (int it = 0; it < BF_GOLDEN; it++) {
+          const double a = hi - gr * (hi - lo), b = lo + gr * (hi - lo);
+          q[j] = a;
+          const double va = bf_value(c, q);
+          q[j] = b;
+          const double vb = bf_value(c, q);
+          if (va >= vb) hi = b;
+          else lo = a;
+        }
+        q[j] = 0.5 * (lo + hi);
+        const double vn = bf_value(c, q);
+        if (vn > cur) {
+          p[j] = q[j];
+          cur = vn;
+        }
+      }
+    if (cur > best) best = cur;
+  }
+  return best;
+}
+
+int orc_bruteforce(const orc_problem *pr, double *best_ee, int64_t *n_assign, int64_t *best_index) {
+  if (!pr || !best_ee || !pr->G || pr->Ks != 0 || pr->M < 1 || pr->M > 8 || pr->N < 1 || pr->K < 1 ||
+      pr->K > 6 || pr->l < 1 || pr->l > 3 || (int64_t)pr->N * pr->M * pr->l > BF_MAXL)
+    return 1;
+  inst_t I;
+  memset(&I, 0, sizeof(I));
+  I.M = pr->M; I.N = pr->N; I.K = pr->K; I.Ks = 0; I.Ke = pr->K; I.l = pr->l;
+  I.G = pr->G; I.pmax = pr->pmax; I.eta = pr->eta;
+  I.sigma = pr->N0_w_per_hz * pr->Bn_hz;
+  double mask[8], w[64];
+  I.mask = mask;
+  I.w = w;
+  I.Pconst = 0.0;
+  for (int m = 0; m < I.M; m++) {
+    mask[m] = pr->pmax[m] / I.N;
+    I.Pconst += pr->Pc[m] + pr->Pf[m];
+  }
+  for (int t = 0; t < I.M * I.K; t++) w[t] = pr->w ? pr->w[t] : 1.0;
+  const int M = I.M, N = I.N, K = I.K, l = I.l, NM = N * M;
+  int64_t nA = 1;
+  for (int k = 0; k < K; k++) nA *= (M + 1);
+  double best = 0.0;
+  int64_t idx = 0, bidx = -1;
+  int A[8];
+  /* subsets of a user list of size <= l, by size then lexicographic */
+  int subs[64][64][4], nsub[64], ssz[64][64];
+  for (int64_t a = 0; a < nA; a++) {
+    int64_t r = a;
+    for (int k = 0; k < K; k++) { A[k] = (int)(r % (M + 1)) - 1; r /= (M + 1); }
+    int64_t nch = 1;
+    for (int nm = 0; nm < NM; nm++) {
+      const int m = nm % M;
+      int users[8], cnt = 0;
+      for (int k = 0; k < K; k++) if (A[k] == m) users[cnt++] = k;
+      int ns = 0;
+      for (int sz = 0; sz <= (cnt < l ? cnt : l); sz++) {
+        int comb[4];
+        for (int i = 0; i < sz; i++) comb[i] = i;
+        for (;;) {
+          for (int i = 0; i < sz; i++) subs[nm][ns][i] = users[comb[i]];
+          ssz[nm][ns] = sz;
+          ns++;
+          int i = sz - 1;
+          while (i >= 0 && comb[i] == cnt - sz + i) i--;
+          if (i < 0) break;
+          comb[i]++;
+          for (int j2 = i + 1; j2 < sz; j2++) comb[j2] = comb[j2 - 1] + 1;
+        }
+      }
+      nsub[nm] = ns;
+      nch *= ns;
+    }
+    for (int64_t ch = 0; ch < nch; ch++) {
+      bf_link L[BF_MAXL];
+      int nl = 0, served[8] = {0};
+      int64_t rr = ch;
+      /* digits: (n, m) in (n, m) order with n slowest, so the last (n, m) varies fastest */
+      int digit[64];
+      for (int nm = NM - 1; nm >= 0; nm--) { digit[nm] = (int)(rr % nsub[nm]); rr /= nsub[nm]; }
+      for (int nm = 0; nm < NM; nm++)
+        for (int i = 0; i < ssz[nm][digit[nm]]; i++) {
+          L[nl].n = nm / M; L[nl].m = nm % M; L[nl].k = subs[nm][digit[nm]][i];
+          served[L[nl].k] = 1;
+          nl++;
+        }
+      int ok = nl > 0;
+      for (int k = 0; k < K && ok; k++) if (A[k] >= 0 && !served[k]) ok = 0;
+      if (!ok) continue;
+      bf_ctx c = {&I, L, nl};
+      const double v = bf_search(&c);
+      if (v > best) { best = v; bidx = idx; }
+      idx++;
+    }
+  }
+  *best_ee = best;
+  if (n_assign) *n_assign = idx;
+  if (best_index) *best_index = bidx;
+  return 0;
+}

@@ -75,6 +75,15 @@ typedef struct {
 
 int orc_solve(const orc_problem *pr, const orc_params *par, orc_result *out);
 
+/* Global-optimum comparator (stands in for Sec. IV-B's monotonic
+ * optimisation on small instances): the best EE over every assignment (RRH
+ * choice and per-(n, m) user subsets of at most l), powers by multi-start
+ * coordinate golden-section search under C12 and C14 (hcran_oracle.c gives
+ * the exact order).  Elastic users only (Ks = 0); M <= 8, K <= 6, l <= 3,
+ * N*M*l <= 16.  *n_assign = assignments searched, *best_index = the
+ * enumeration index of the best one (-1 if none); returns 1 on a bad problem. */
+int orc_bruteforce(const orc_problem *pr, double *best_ee, int64_t *n_assign, int64_t *best_index);
+
 /* closed-form pieces, exposed so that tests can pin them on their own */
 double orc_psi(double T_s, double lambda_pps, double zbar_bits, double Bn_hz);   /* C9 */
 void orc_scale_coeffs(double z0, double *alpha, double *beta);                   /* SCALE bound */

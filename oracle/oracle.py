@@ -69,6 +69,8 @@ def _load():
         lib.orc_psi.restype = C.c_double
         lib.orc_scale_coeffs.argtypes = [C.c_double, _dp, _dp]
         lib.orc_scale_coeffs.restype = None
+        lib.orc_bruteforce.argtypes = [C.POINTER(_Problem), _dp, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
+        lib.orc_bruteforce.restype = C.c_int
         _lib = lib
     return _lib
 
@@ -82,6 +84,32 @@ def scale_coeffs(z0: float):
     a, b = C.c_double(), C.c_double()
     _load().orc_scale_coeffs(z0, C.byref(a), C.byref(b))
     return a.value, b.value
+
+
+def _problem(inst, keep):
+    def d(x):
+        a = np.ascontiguousarray(x, dtype=np.float64)
+        keep.append(a)
+        return _ptr(a, _dp)
+    G = np.ascontiguousarray(inst.G, dtype=np.float32)
+    keep.append(G)
+    Ks = inst.Ks
+    return _Problem(inst.M, inst.N, inst.K, Ks, inst.l, d(inst.pmax), d(inst.eta), d(inst.Pc), d(inst.Pf),
+                    float(inst.Bn_hz), float(inst.N0_w_per_hz),
+                    d(inst.T_s if Ks else np.zeros(1)), d(inst.lambda_pps if Ks else np.ones(1)),
+                    float(inst.zbar_bits), d(inst.w) if inst.w is not None else None, _ptr(G, _fp))
+
+
+def bruteforce(inst):
+    """(best EE, assignments searched, index of the best) of the global-optimum
+    comparator (elastic users only; see hcran_oracle.h)."""
+    lib = _load()
+    keep = []
+    pr = _problem(inst, keep)
+    ee, na, bi = C.c_double(), C.c_int64(), C.c_int64()
+    if lib.orc_bruteforce(C.byref(pr), C.byref(ee), C.byref(na), C.byref(bi)) != 0:
+        raise ValueError("bruteforce rejected the problem")
+    return ee.value, na.value, bi.value
 
 
 @dataclasses.dataclass

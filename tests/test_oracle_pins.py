@@ -493,3 +493,59 @@ def test_perturbation_ensemble_is_opt_in_and_small_on_a_stable_instance():
     for r in members[1:]:
         assert np.array_equal(r.S, a.S)
         assert abs(r.ee - a.ee) / a.ee < 1e-6
+
+
+# ---------------------------------------------------------------- global-optimum comparator
+
+def _count_assignments(M, N, K, l):
+    """Number of assignments by a direct itertools enumeration: RRH choice per
+    user, per-(n, m) subsets of at most l of its users, every user with an
+    RRH on at least one link."""
+    import itertools
+    tot = 0
+    for A in itertools.product(range(-1, M), repeat=K):
+        per = []
+        for n in range(N):
+            for m in range(M):
+                users = [k for k in range(K) if A[k] == m]
+                per.append([c for r in range(0, min(l, len(users)) + 1) for c in itertools.combinations(users, r)])
+        for ch in itertools.product(*per):
+            served = {k for sub in ch for k in sub}
+            if served and all(A[k] < 0 or k in served for k in range(K)):
+                tot += 1
+    return tot
+
+
+@pytest.mark.parametrize("shape", [(2, 1, 3, 2), (1, 2, 3, 2), (3, 2, 3, 2), (2, 2, 3, 1)])
+def test_bruteforce_enumerates_every_assignment(shape):
+    from hcran_inputs import make_instance
+    M, N, K, l = shape
+    inst = make_instance(800001, M=M, N=N, K=K, Ks=0, l=l)
+    ee, n_assign, best = oracle.bruteforce(inst)
+    assert n_assign == _count_assignments(M, N, K, l)
+    assert 0 <= best < n_assign and ee > 0
+
+
+@pytest.mark.parametrize("gain,pmax", [(2e-14, 10.0), (5e-15, 0.5)])
+def test_bruteforce_single_link_is_the_lambert_w_optimum(gain, pmax):
+    inst = micro([[[gain]]], pmax=[pmax], eta=[3.0], Pc=[2.0], Pf=[1.0])
+    ee, n_assign, _ = oracle.bruteforce(inst)
+    g = float(np.float32(gain)) / SIGMA
+    p_star = lambert_ee_opt(g, 3.0, 3.0, pmax)
+    assert n_assign == 1
+    assert ee == pytest.approx(math.log2(1 + g * p_star) / (3.0 + 3.0 * p_star), rel=1e-9)
+
+
+@pytest.mark.parametrize("shape,seed", [((1, 2, 3), 5), ((2, 1, 3), 6)])
+def test_bruteforce_agrees_with_the_random_start_search(shape, seed):
+    """The comparator's deterministic search and the random-start search of
+    brute_force_ee (an independent implementation on the exact model) find
+    the same optimum on the micro instances, and the method stays below it."""
+    N, M, K = shape
+    rng = np.random.default_rng(seed)
+    G = (10.0 ** rng.uniform(-14.0, -12.5, size=(N, M, K))).astype(np.float32)
+    inst = micro(G, l=2, pmax=[1.0] * M, eta=[2.0] * M)
+    ee, _, _ = oracle.bruteforce(inst)
+    bf = brute_force_ee(inst)
+    assert ee == pytest.approx(bf, rel=1e-3)
+    assert oracle.solve(inst, Tolerances()).ee <= ee * (1 + 1e-6)
