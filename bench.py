@@ -285,6 +285,12 @@ def run_gpu(args):
     large = None
     if args.large and world == 1:
         large = large_leg(dev)
+    optimum = None
+    if not args.no_scenarios and world == 1:
+        try:
+            optimum = optimum_leg(dev)
+        except Exception as e:  # the main bench line stands on its own
+            optimum = {"error": "%s: %s" % (type(e).__name__, e)}
 
     if rank == 0:
         per_step_ms = ms_max / args.steps
@@ -351,6 +357,8 @@ def run_gpu(args):
             out["scenarios"] = scen
         if large:
             out["large"] = large
+        if optimum:
+            out["optimum_gap"] = optimum
         print(json.dumps(out), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -396,6 +404,37 @@ def large_leg(dev, count=256):
     del g
     torch.cuda.empty_cache()
     return out
+
+
+def optimum_leg(dev):
+    """The gap of the method to the optimum (Sec. IV-B's role): the 256
+    instances of the optimum workload (1 HPN + 2 LPNs, 2 subcarriers, 3
+    elastic users, l = 2; 954 assignments each) through the GPU brute-force
+    comparator and through the method's GPU solve.  Reports the comparator's
+    time and the distribution of EE(method) / EE(optimum)."""
+    import torch
+    from hcran_inputs import WORKLOADS, make_workload, pack_batch
+    from paper_1803_07772_gb300 import Solver, make_tol
+    from paper_1803_07772_gb300.hcran import bruteforce
+    name = "optimum-3x2x3"
+    insts = make_workload(name)
+    gains, offs = pack_batch(insts)
+    g = torch.from_numpy(gains).to(dev)
+    bruteforce(insts, g)  # warm-up
+    t0 = time.perf_counter()
+    ee_opt, _, na = bruteforce(insts, g)
+    bf_s = time.perf_counter() - t0
+    stream = torch.cuda.Stream(dev)
+    with torch.cuda.stream(stream):
+        s = Solver(insts, gain_offsets=offs, device=str(dev), stream=stream)
+    s.solve(g, make_tol(WORKLOADS[name]["tol"]))
+    ee = s.summary()["ee"]
+    s.close()
+    r = ee / ee_opt
+    return {"workload": name, "instances": len(insts), "assignments_per_instance": int(na),
+            "comparator_seconds": bf_s, "comparator_assignments_per_s": len(insts) * na / bf_s,
+            "method_over_optimum": {"min": float(r.min()), "median": float(np.median(r)), "mean": float(r.mean()),
+                                    "max": float(r.max()), "within_1pct": float(np.mean(r >= 0.99))}}
 
 
 def scenario_leg(dev):

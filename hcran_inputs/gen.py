@@ -226,6 +226,10 @@ def _scen_hpn(i: int) -> Instance:
                          per_rrh=dict(pmax=[40.0] * 2, eta=[4.0] * 2, Pc=[10.0] * 2, Pf=[0.0] * 2), **_SCEN_TRAFFIC)
 
 
+def _optimum(i: int) -> Instance:
+    return make_instance(800000 + i, M=3, N=2, K=3, Ks=0, l=2)
+
+
 WORKLOADS: Dict[str, dict] = {
     # 1 HPN + 2 LPNs, 8 subcarriers, 4 elastic + 2 streaming users, l = 2
     "small-3x8x6": dict(make=_small, count=1, tol=Tolerances()),
@@ -236,6 +240,9 @@ WORKLOADS: Dict[str, dict] = {
     "batch-4096-uneven": dict(make=_batch, count=4096, tol=Tolerances()),
     # 1 HPN + 32 LPNs, 1024 subcarriers, 384 elastic + 128 streaming, l = 4
     "large-33x1024x512": dict(make=_large, count=256, tol=Tolerances()),
+    # small H-CRAN instances whose optimum the brute-force comparator finds:
+    # 1 HPN + 2 LPNs, 2 subcarriers, 3 elastic users, l = 2 (954 assignments)
+    "optimum-3x2x3": dict(make=_optimum, count=256, tol=Tolerances()),
     # the architectures of Sec. VI (same seeds and users in each)
     "scenario-hcran-noma": dict(make=_scen_hcran, count=256, tol=Tolerances()),
     "scenario-hcran-oma": dict(make=_scen_hcran_oma, count=256, tol=Tolerances()),

@@ -270,6 +270,35 @@ int hcran_solve_warm(hcran_t h, const float *gains_dev, const hcran_tol *tol, vo
 
 void hcran_destroy(hcran_t h);
 
+/* ---- global-optimum comparator -----------------------------------------
+ * The paper compares its method with the optimum found by monotonic
+ * optimisation (Sec. IV-B).  For small instances this computes that optimum's
+ * stand-in by enumeration on the GPU: the best EE = R/P over every
+ * assignment and over the powers.
+ *  - Assignments: every RRH choice A_k in {-1 .. M-1} (A as a number in base
+ *    M+1, user 0 the fastest digit, digit d meaning A_k = d - 1) and, on every
+ *    (n, m) in (n, m) order with n slowest, every subset of the users of m of
+ *    at most l members (listed by size, then lexicographically; the last
+ *    (n, m) varies fastest), keeping those where every user with A_k >= 0 has
+ *    at least one link.  best_index counts in that order.
+ *  - Powers: coordinate golden-section search in [1e-6 mask, mask] from three
+ *    starts p = f mask (f = 0.1, 0.4, 1), 8 sweeps over the links, 40 steps
+ *    per link; a point breaking C12 or C14 (pairs of one (m, n) in SIC order)
+ *    is infeasible.  FP64.
+ *  - cfgs: n instances of one shape (M <= 8, K <= 6, l <= 3, N*M*l <= 16),
+ *    elastic users only (Ks = 0); host memory read during the call.
+ *  - gains_dev: float32 Gamma[n][m][k], instance b at element
+ *    b * ((N*M*K + 3) / 4 * 4), device memory, 16-byte aligned.
+ *  - workspace_dev: hcran_bf_workspace_size() bytes, 256-byte aligned,
+ *    owned by the caller; the library allocates nothing.
+ *  - Enqueues on `stream`, synchronises it, and writes best_ee[n] (0 when no
+ *    assignment is feasible) and best_index[n] (-1 then; may be NULL) to host
+ *    memory.  HCRAN_EINVAL for a bad or mixed shape, HCRAN_ECUDA on a CUDA
+ *    error. */
+int hcran_bf_workspace_size(const hcran_config *cfgs, int32_t n, uint64_t *bytes, int64_t *n_assign);
+int hcran_bruteforce(const hcran_config *cfgs, int32_t n, const float *gains_dev, void *workspace_dev,
+                     void *stream, double *best_ee, int64_t *best_index);
+
 /* ---- allocation-free single-instance solve ----------------------------
  * The paper has no counterpart: this entry point exists for callers that
  * cannot allocate device memory (a process whose device memory belongs to
