@@ -236,3 +236,15 @@ def test_large_instance_matches_oracle_at_fixed_counts():
     assert g["iters"] == o.iters
     compare(inst, g, o, "large fixed-count")
 
+
+
+def test_large_instance_first_dinkelbach_iteration_under_its_stop_rules():
+    """The 33 x 1024 x 512 shape through one whole Dinkelbach iteration with
+    the workload's own SCALE and dual stop rules (varpi_1, varpi_2, S = 50,
+    V = 200): the plain bar, with the tiers of tests.parity."""
+    inst = make_workload("large-33x1024x512", count=1)[0]
+    tol = copy.copy(WORKLOADS["large-33x1024x512"]["tol"])
+    tol.max_dinkelbach = 1
+    g = gpu_solve([inst], tol)[0]
+    tier, rep = hold(inst, g, tol, "large, one Dinkelbach iteration")
+    assert tier in ("plain", "tie", "stop"), rep
