@@ -208,10 +208,15 @@ int hcran_get_schedule(hcran_t h, int32_t *cluster_size);
 
 /* Replace the schedule: cluster_size[b] in 1 .. 8 (a cluster of that
  * many CTAs with the dual-loop state resident in their shared memory; at
- * least one subcarrier per CTA, and the state must fit) or 0 (one CTA
- * streaming from global memory).  An instance whose class would exceed
- * shared memory moves on to a larger cluster (hcran_get_schedule reports the
- * result).  The next solve uploads the new plan to its workspace.  Returns
+ * least one subcarrier per CTA, and the state must fit), 0 (one CTA
+ * streaming each subcarrier's state from global memory, staged as the
+ * planner sees fit) or -T, T in 1 .. 4 (the same, with the CTA's warps in T
+ * teams that each stage one subcarrier at a time: the planner's choice when
+ * the double buffers of every warp do not fit; every negative entry must
+ * give the same T, and the teams' buffers must fit).  An instance whose
+ * class would exceed shared memory moves on to a larger cluster
+ * (hcran_get_schedule reports the result, 0 for every streamed instance).
+ * The next solve uploads the new plan to its workspace.  Returns
  * HCRAN_EINVAL (schedule unchanged) on a NULL argument or an infeasible
  * size. */
 int hcran_set_schedule(hcran_t h, const int32_t *cluster_size);

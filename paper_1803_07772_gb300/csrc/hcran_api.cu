@@ -47,6 +47,7 @@ struct hcran_s {
   bool plan_dirty = false;  // descriptors / order changed since they were uploaded
   int64_t spin_limit = 0;        // tries of a bounded device wait (0: the default)
   int32_t stall_instance = -1;   // test of the failure path (hcran_set_wait_limit)
+  int32_t stream_teams = 0;      // > 0: the streamed class sweeps with this many teams (hcran_set_schedule)
   // captured launch sequence of hcran_solve_graph and the arguments it was captured for
   cudaGraphExec_t graph = nullptr;
   const void *graph_gains = nullptr, *graph_ws = nullptr;
@@ -106,6 +107,15 @@ static int build_classes(hcran_s *h) {
   {  // streamed class: staging when the double buffers fit, else global reads
     LaunchClass &L = h->classes[kNumClasses - 1];
     if (L.count > 0 && plan_kdims(L.kd, int64_t(1) << 40) != 0) return 1;
+    if (L.count > 0 && h->stream_teams > 0) {  // team sweeps requested by hcran_set_schedule
+      KDims t = L.kd;
+      t.resident = 0;
+      t.res_floats = 0;
+      t.staged = 1;
+      t.teams = h->stream_teams;
+      if (dyn_smem_bytes(t) > kMaxDynSmem) return 1;
+      L.kd = t;
+    }
   }
   for (int32_t b = 0; b < n; b++) {
     InstDesc &d = h->descs[b];
@@ -639,10 +649,13 @@ extern "C" int hcran_get_schedule(hcran_t h, int32_t *cluster_size) {
 extern "C" int hcran_set_schedule(hcran_t h, const int32_t *cluster_size) {
   if (!h || !cluster_size) return HCRAN_EINVAL;
   std::vector<int32_t> cls(h->n);
+  int32_t teams = 0;
   for (int32_t b = 0; b < h->n; b++) {
     const InstDesc &d = h->descs[b];
     const int C = cluster_size[b];
-    if (C == 0) {
+    if (C <= 0) {
+      if (C < -4 || (C < 0 && teams != 0 && teams != -C)) return HCRAN_EINVAL;
+      if (C < 0) teams = -C;
       cls[b] = kNumClasses - 1;
       continue;
     }
@@ -654,9 +667,12 @@ extern "C" int hcran_set_schedule(hcran_t h, const int32_t *cluster_size) {
     cls[b] = k;
   }
   const std::vector<int32_t> keep = h->cls;
+  const int32_t keep_teams = h->stream_teams;
   h->cls = cls;
+  h->stream_teams = teams;
   if (build_classes(h) != 0) {
     h->cls = keep;
+    h->stream_teams = keep_teams;
     build_classes(h);
     return HCRAN_EINVAL;
   }

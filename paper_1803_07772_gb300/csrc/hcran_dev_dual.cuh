@@ -4,7 +4,8 @@
 // in staged mode the warp's first lane prefetches the next subcarrier's SIC
 // multipliers, slab rows and slot arrays into the other shared staging buffer
 // with one-dimensional bulk copies (cp.async.bulk) completed on an mbarrier,
-// while the lanes work on the current one.
+// while the lanes work on the current one.  When the double buffers of every
+// warp do not fit, teams of warps share them (hcran_dev_team.cuh).
 #pragma once
 #include "hcran_dev_link.cuh"
 
@@ -30,6 +31,12 @@ __device__ __forceinline__ void issue_stage(const Ctx &c, Shared &sh, const KDim
                                     c.gown + o, c.ginv + o, c.wslot + o};
   for (int i = 0; i < kStagedArrays; i++) bulk_g2s(f + i * kd.Upmax, src[i], fa, bar);
 }
+
+}  // namespace hcran
+
+#include "hcran_dev_team.cuh"
+
+namespace hcran {
 
 // One sweep of the warp over its subcarriers.  The caller fences the proxies
 // and synchronises the block before it (bulk copies read what the previous
@@ -93,7 +100,8 @@ __device__ void link_all(const Ctx &c, Shared &sh, float *dyn, const KDims &kd, 
                          float delta, unsigned &phase, unsigned &pending) {
   fence_proxy_async();
   __syncthreads();
-  sweep<MODE>(c, sh, dyn, kd, szeta, delta, phase, pending);
+  if (kd.teams > 0) team_sweep<MODE>(c, sh, dyn, kd, szeta, delta, phase, pending);
+  else sweep<MODE>(c, sh, dyn, kd, szeta, delta, phase, pending);
   __syncthreads();
 }
 
@@ -115,13 +123,17 @@ __device__ int dual_loop(const Ctx &c, Shared &sh, float *dyn, const KDims &kd, 
     // projected subgradient step on xi' (C12) and zeta' (C13 hat) at p^v:
     // steps in FP32, accumulated into the FP64 multiplier values
     const float delta = rsqrtf((float)v + 1.f);
-    const int wstride = warp_stride(kd);
-    const WarpBuf w0 = warp_buf(dyn, kd, 0);
+    // the partials of the warps (warp sweeps) or of the teams (team sweeps)
+    const int parts = kd.teams > 0 ? kd.teams : kWarps;
+    const int wstride = kd.teams > 0 ? team_stride(kd) : warp_stride(kd);
+    const float *wp0 = kd.teams > 0 ? team_buf(dyn, kd, 0).wp : warp_buf(dyn, kd, 0).wp;
+    const float *wr0 = kd.teams > 0 ? team_buf(dyn, kd, 0).wr : warp_buf(dyn, kd, 0).wr;
+    const float *wa0 = kd.teams > 0 ? team_buf(dyn, kd, 0).wa : warp_buf(dyn, kd, 0).wa;
     for (int t = threadIdx.x; t < c.M + c.Ks; t += kThreads) {
       if (t < c.M) {
         const int m = t;
         float tot = 0.f;
-        for (int i = 0; i < kWarps; i++) tot += w0.wp[i * wstride + m];
+        for (int i = 0; i < parts; i++) tot += wp0[i * wstride + m];
         const float pm = (float)c.pmax[m];
         const float step = delta * ((tot - pm) / pm) / (LN2F * sh.maskf[m]);
         double x = c.xi[m];
@@ -134,9 +146,9 @@ __device__ int dual_loop(const Ctx &c, Shared &sh, float *dyn, const KDims &kd, 
       } else {
         const int ks = t - c.M;
         float r = 0.f, as = 0.f;
-        for (int i = 0; i < kWarps; i++) {
-          r += w0.wr[i * wstride + ks];
-          as += w0.wa[i * wstride + ks];
+        for (int i = 0; i < parts; i++) {
+          r += wr0[i * wstride + ks];
+          as += wa0[i * wstride + ks];
         }
         const float x = delta * fminf(fmaxf((sh_psi(c, ks) - r) / fmaxf(as, (float)kZetaAsumMin), -1.f), 1.f);
         const double z = fmin(fmax(c.zeta[ks] * (double)exp2f(x), kZetaMin), kZetaMax);
@@ -147,7 +159,9 @@ __device__ int dual_loop(const Ctx &c, Shared &sh, float *dyn, const KDims &kd, 
     fence_proxy_async();
     __syncthreads();
     const long long t2 = clock64();
-    const float dl = sweep<kFused>(c, sh, dyn, kd, szeta, rsqrtf((float)v + 2.f), phase, pending);
+    const float dl = kd.teams > 0
+                         ? team_sweep<kFused>(c, sh, dyn, kd, szeta, rsqrtf((float)v + 2.f), phase, pending)
+                         : sweep<kFused>(c, sh, dyn, kd, szeta, rsqrtf((float)v + 2.f), phase, pending);
     if (lane == 0) sh.redf[warp] = dl;
     v++;
     __syncthreads();

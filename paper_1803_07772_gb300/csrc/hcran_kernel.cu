@@ -355,9 +355,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     solve_instance(sc, sh, dyn, kd, tol, outs + b, b, phase, pending);
   }
   // never leave a bulk copy in flight (bounded; set only after a timed-out wait)
+  const int bi = kd.teams > 0 ? team_of(kd, warp) : warp;  // the barriers this thread's copies complete on
   for (int bb = 0; bb < 2; bb++)
     if (pending & (1u << bb)) {
-      mbar_wait(&sh.bar[warp][bb], (phase >> bb) & 1u, sh.spin_limit);
+      mbar_wait(&sh.bar[bi][bb], (phase >> bb) & 1u, sh.spin_limit);
     }
 }
 

@@ -173,6 +173,9 @@ struct KDims {
   int staged;   // 1: per-subcarrier state double-buffered in shared memory by bulk copies
   int resident; // 1: the dual loop keeps the CTA's subcarrier state in shared memory
   int res_floats;  // resident region (floats), the largest instance of the launch
+  int teams;    // > 0: the sweeps run on this many teams of kWarps / teams warps, one
+                // subcarrier per team at a time, each team double-buffering its
+                // subcarriers' state by bulk copies (needs staged = 1)
 };
 // per-warp working buffers (floats)
 HCRAN_HD int warp_work_floats(const KDims &k) {
@@ -189,6 +192,19 @@ HCRAN_HD int stage_buf_floats(const KDims &k) {
 HCRAN_HD int warp_buf_floats(const KDims &k) {
   return int(al4(warp_work_floats(k))) + (k.staged ? 2 * stage_buf_floats(k) : 0);
 }
+// Team sweeps: a team of kWarps / teams warps works on one subcarrier at a
+// time.  Per team: slot arrays p, pi, X, k [Upmax]; per-RRH totals, price
+// sums, SIC+, SIC-, power partials [Mmax]; the SIC multipliers of the
+// subcarrier densely and as a compact list of the nonzero ones (values and
+// items) [Mmax * NPmax]; three partial sums per thread; the streaming rate and
+// alpha partials [KSmax]; a counter; then the two staging buffers.
+HCRAN_HD int team_threads(const KDims &k) { return (kWarps / (k.teams > 0 ? k.teams : 1)) * 32; }
+HCRAN_HD int team_work_floats(const KDims &k) {
+  const int np = k.NPmax > 0 ? k.NPmax : 1;
+  return int(al4(4 * k.Upmax + 5 * k.Mmax + 3 * k.Mmax * np + 3 * team_threads(k) +
+                 2 * (k.KSmax > 0 ? k.KSmax : 1) + 4));
+}
+HCRAN_HD int team_stride(const KDims &k) { return team_work_floats(k) + 2 * stage_buf_floats(k); }
 // Resident dual loop: shared-memory state of Nc subcarriers (structure of
 // arrays): slab [Nc][M][Rs] (row stride Rs = Up, or Up + 4 when Up / 4 is
 // even, so that lanes reading consecutive rows as float4 hit distinct banks);
@@ -228,17 +244,19 @@ HCRAN_HD int64_t dyn_head_floats(const KDims &k) {
 }
 HCRAN_HD int warp_stride(const KDims &k) { return warp_buf_floats(k); }
 HCRAN_HD int64_t dyn_smem_bytes(const KDims &k) {
-  const int64_t w = int64_t(kWarps) * warp_stride(k);
+  const int64_t w = k.teams > 0 ? int64_t(k.teams) * team_stride(k) : int64_t(kWarps) * warp_stride(k);
   const int64_t r = k.resident ? int64_t(k.res_floats) : 0;
   return 4 * (dyn_head_floats(k) + (w > r ? w : r));
 }
 
 // Schedule of a launch: the resident dual loop when the largest instance's
-// state fits shared memory, else bulk-copy staging of each subcarrier when the
-// double buffers fit, else global reads.  Returns nonzero when even the
+// state fits shared memory; else bulk-copy staging of each subcarrier, by
+// every warp when its double buffers fit, else by as many teams of warps
+// (4, 3, 2, 1) as fit; else global reads.  Returns nonzero when even the
 // per-warp buffers do not fit.
 inline int plan_kdims(KDims &k, int64_t res_need) {
   k.staged = 0;
+  k.teams = 0;
   k.resident = 1;
   k.res_floats = int(res_need < (int64_t(1) << 30) ? res_need : (int64_t(1) << 30));
   if (dyn_smem_bytes(k) <= kMaxDynSmem) return 0;
@@ -246,6 +264,11 @@ inline int plan_kdims(KDims &k, int64_t res_need) {
   k.res_floats = 0;
   k.staged = 1;
   if (dyn_smem_bytes(k) <= kMaxDynSmem) return 0;
+  for (int t = 4; t >= 1; t--) {
+    k.teams = t;
+    if (dyn_smem_bytes(k) <= kMaxDynSmem) return 0;
+  }
+  k.teams = 0;
   k.staged = 0;
   return dyn_smem_bytes(k) <= kMaxDynSmem ? 0 : 1;
 }
@@ -261,6 +284,7 @@ inline KDims resident_kdims(int M, int l, int Ks, int N, int C) {
   k.NPPmax = pair_stride(M, l);
   k.KSmax = Ks;
   k.staged = 0;
+  k.teams = 0;
   k.resident = 1;
   const int64_t r = res_floats(M, l, Ks, (N + C - 1) / C);
   k.res_floats = int(r < (int64_t(1) << 30) ? r : (int64_t(1) << 30));

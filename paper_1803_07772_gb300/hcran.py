@@ -201,7 +201,8 @@ class Solver:
             C.c_void_p(self.workspace.data_ptr()), C.c_void_p(self.stream.cuda_stream)))
 
     def set_schedule(self, cluster_size):
-        """Cluster size per instance (1 .. 8; 0: one CTA streaming from global memory)."""
+        """Cluster size per instance (1 .. 8; 0: one CTA streaming from global memory;
+        -T: streamed with T teams of warps, T in 1 .. 4)."""
         a = np.ascontiguousarray(cluster_size, dtype=np.int32)
         _check("hcran_set_schedule", self.lib.hcran_set_schedule(self.h, a.ctypes.data_as(_ip)))
 

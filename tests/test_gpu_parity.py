@@ -65,7 +65,7 @@ def test_config_matches_plain_oracle(name):
     assert g["status"] == o.status == 0
 
 
-@pytest.mark.parametrize("v", [1, 5, 60])
+@pytest.mark.parametrize("v", [1, 5, 60, 200])
 def test_dual_steps_match_at_fixed_E(v):
     """One selection then exactly v dual iterations of one SCALE pass at a
     fixed E: isolates the KKT power and subgradient arithmetic."""
@@ -82,6 +82,7 @@ def test_dual_steps_match_at_fixed_E(v):
           "zeta rel", np.max(np.abs(g["zeta"] - o.zeta) / o.zeta))
     assert rel.max() < 1e-4
     assert np.allclose(g["zeta"], o.zeta, rtol=1e-4)
+    assert np.allclose(g["xi"], o.xi, rtol=1e-4, atol=1e-6 * max(1.0, float(np.max(np.abs(o.xi)))))
 
 
 def test_algorithm1_matches_at_fixed_E():
@@ -206,6 +207,27 @@ def test_every_cluster_size_matches_oracle_at_fixed_counts():
             r = s.get(i)
             assert r["iters"] == o.iters
             compare(inst, r, o, "schedule %d (got %d)" % (want, s.schedule()[i]))
+
+
+def test_team_sweeps_match_oracle_at_fixed_counts():
+    """The streamed schedule with its warps in 1 to 4 teams that each stage
+    one subcarrier at a time (the planner's choice for instances whose warp
+    buffers do not fit, such as the 33 x 1024 x 512 shape), forced on batch
+    instances and the medium configuration: fixed iteration counts, every
+    selected power held to the strict bar."""
+    insts = _batch_subset(count=3) + make_workload("medium-9x64x48")
+    tol = Tolerances(tol_dinkelbach=0.0, tol_scale=0.0, tol_dual=0.0,
+                     max_dinkelbach=2, max_scale=3, max_dual=40)
+    orcs = [oracle.solve(i, tol) for i in insts]
+    from paper_1803_07772_gb300 import make_tol
+    s, g = _solver(insts)
+    for teams in [1, 2, 3, 4]:
+        s.set_schedule(np.full(len(insts), -teams, np.int32))
+        s.solve(g, make_tol(tol, tie_eps=TIE_BAND))
+        for i, (inst, o) in enumerate(zip(insts, orcs)):
+            r = s.get(i)
+            assert r["iters"] == o.iters
+            compare(inst, r, o, "%d teams" % teams)
 
 
 def test_autotuned_schedule_is_valid_and_matches_oracle():
