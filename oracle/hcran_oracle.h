@@ -84,6 +84,29 @@ int orc_solve(const orc_problem *pr, const orc_params *par, orc_result *out);
  * enumeration index of the best one (-1 if none); returns 1 on a bad problem. */
 int orc_bruteforce(const orc_problem *pr, double *best_ee, int64_t *n_assign, int64_t *best_index);
 
+/* Paper-literal penalty form of the selection constraints (C10, C11 kept
+ * with multipliers theta, theta' instead of the explicit selection; see
+ * hcran_penalty.c for the readings and the index order of the arrays).
+ * Elastic users only (Ks = 0), unit weights, M <= 8; rho_rel in (0, 1) sets
+ * rho_1 = rho_rel^2 mask_m mask_m' and rho_2 = rho_rel^(l+1) mask_m^(l+1).
+ * Returns 1 on a bad problem, 2 when out of memory. */
+typedef struct {
+  double *p;                   /* [N*M*K] W, every (n, m, k) link (may be NULL) */
+  double *alpha;               /* [N*M*K] SCALE coefficient after the last pass (may be NULL) */
+  double *xi;                  /* [M] (may be NULL) */
+  double *theta;               /* [n_theta] C10 multipliers (may be NULL) */
+  double *theta2;              /* [n_theta2] C11 multipliers (may be NULL) */
+  double ee, R, P;
+  int32_t iters[3];
+  int32_t status;              /* bit 0: the Dinkelbach cap was reached */
+  double slack_power_min;      /* min_m (pmax - sum p)/pmax */
+  double c10_max, c11_max;     /* largest C10 / C11 product relative to rho_1 / rho_2 */
+  double slack_sic_max;        /* max Omega_bar / mask over pairs of links above rho_rel mask */
+  int32_t n_theta, n_theta2;
+} orc_pen_result;
+
+int orc_penalty_solve(const orc_problem *pr, const orc_params *par, double rho_rel, orc_pen_result *out);
+
 /* closed-form pieces, exposed so that tests can pin them on their own */
 double orc_psi(double T_s, double lambda_pps, double zbar_bits, double Bn_hz);   /* C9 */
 void orc_scale_coeffs(double z0, double *alpha, double *beta);                   /* SCALE bound */

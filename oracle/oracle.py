@@ -15,6 +15,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "hcran_oracle.c")
+_SRCS = [_SRC, os.path.join(_HERE, "hcran_penalty.c")]
 _OUT = os.path.join(_HERE, "_build", "liborc.so")
 _lib = None
 
@@ -48,13 +49,22 @@ class _Result(C.Structure):
                 ("n_ties", C.c_int32), ("n_scale_traced", C.c_int32)]
 
 
+class _PenResult(C.Structure):
+    _fields_ = [("p", _dp), ("alpha", _dp), ("xi", _dp), ("theta", _dp), ("theta2", _dp),
+                ("ee", C.c_double), ("R", C.c_double), ("P", C.c_double),
+                ("iters", C.c_int32 * 3), ("status", C.c_int32),
+                ("slack_power_min", C.c_double), ("c10_max", C.c_double), ("c11_max", C.c_double),
+                ("slack_sic_max", C.c_double), ("n_theta", C.c_int32), ("n_theta2", C.c_int32)]
+
+
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (strict IEEE: no fast-math, no FMA contraction)."""
-    if force or not os.path.exists(_OUT) or os.path.getmtime(_OUT) < os.path.getmtime(_SRC):
+    newest = max(os.path.getmtime(f) for f in _SRCS + [os.path.join(_HERE, "hcran_oracle.h")])
+    if force or not os.path.exists(_OUT) or os.path.getmtime(_OUT) < newest:
         os.makedirs(os.path.dirname(_OUT), exist_ok=True)
         tmp = _OUT + ".tmp%d" % os.getpid()
         subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
-                               "-o", tmp, _SRC, "-lm"])
+                               "-o", tmp, *_SRCS, "-lm"])
         os.replace(tmp, _OUT)
     return _OUT
 
@@ -71,6 +81,9 @@ def _load():
         lib.orc_scale_coeffs.restype = None
         lib.orc_bruteforce.argtypes = [C.POINTER(_Problem), _dp, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
         lib.orc_bruteforce.restype = C.c_int
+        lib.orc_penalty_solve.argtypes = [C.POINTER(_Problem), C.POINTER(_Params), C.c_double,
+                                          C.POINTER(_PenResult)]
+        lib.orc_penalty_solve.restype = C.c_int
         _lib = lib
     return _lib
 
@@ -200,3 +213,56 @@ def solve(inst, tol=None, q_init: float = 0.0, tie_eps: float = 1e-9,
         ee=res.ee, R=res.R, P=res.P, iters=tuple(res.iters), status=res.status,
         slack_power_min=res.slack_power_min, slack_rate_min=res.slack_rate_min,
         slack_sic_max=res.slack_sic_max, min_margin=res.min_margin, n_ties=res.n_ties)
+
+
+@dataclasses.dataclass
+class PenaltyResult:
+    p: np.ndarray          # [N][M][K]
+    alpha: np.ndarray      # [N][M][K]
+    xi: np.ndarray
+    theta: np.ndarray      # C10 multipliers (hcran_penalty.c gives the order)
+    theta2: np.ndarray     # C11 multipliers
+    ee: float
+    R: float
+    P: float
+    iters: tuple
+    status: int
+    slack_power_min: float
+    c10_max: float
+    c11_max: float
+    slack_sic_max: float
+
+
+def penalty_solve(inst, tol=None, rho_rel: float = 1e-3, q_init: float = 0.0,
+                  max_dinkelbach: Optional[int] = None, max_scale: Optional[int] = None,
+                  max_dual: Optional[int] = None) -> PenaltyResult:
+    """The paper-literal penalty form of C10/C11 (``hcran_penalty.c``) on one
+    elastic-only ``hcran_inputs.Instance``."""
+    from math import comb
+    lib = _load()
+    keep = []
+    pr = _problem(inst, keep)
+    if tol is None:
+        from hcran_inputs import Tolerances
+        tol = Tolerances()
+    Imax = max_dinkelbach if max_dinkelbach is not None else tol.max_dinkelbach
+    Smax = max_scale if max_scale is not None else tol.max_scale
+    Vmax = max_dual if max_dual is not None else tol.max_dual
+    par = _Params(tol.tol_dinkelbach, tol.tol_scale, tol.tol_dual, Imax, Smax, Vmax, q_init, 0.0, 0.0, 0)
+    M, N, K, l = inst.M, inst.N, inst.K, inst.l
+    L = N * M * K
+    n10 = K * (M * (M - 1) // 2) * N * N
+    n11 = N * M * comb(K, l + 1)
+    out = dict(p=np.zeros(L), alpha=np.zeros(L), xi=np.zeros(M), theta=np.zeros(max(n10, 1)),
+               theta2=np.zeros(max(n11, 1)))
+    res = _PenResult()
+    for name, arr in out.items():
+        setattr(res, name, _ptr(arr, _dp))
+    rc = lib.orc_penalty_solve(C.byref(pr), C.byref(par), float(rho_rel), C.byref(res))
+    if rc != 0:
+        raise ValueError("penalty oracle rejected the problem (code %d)" % rc)
+    assert res.n_theta == n10 and res.n_theta2 == n11
+    return PenaltyResult(p=out["p"].reshape(N, M, K), alpha=out["alpha"].reshape(N, M, K), xi=out["xi"],
+                         theta=out["theta"][:n10], theta2=out["theta2"][:n11], ee=res.ee, R=res.R, P=res.P,
+                         iters=tuple(res.iters), status=res.status, slack_power_min=res.slack_power_min,
+                         c10_max=res.c10_max, c11_max=res.c11_max, slack_sic_max=res.slack_sic_max)

@@ -14,6 +14,7 @@ import oracle.oracle as oo
 from tests import test_oracle_pins as pins
 
 SRC = os.path.join(os.path.dirname(oo.__file__), "hcran_oracle.c")
+SRC_PEN = os.path.join(os.path.dirname(oo.__file__), "hcran_penalty.c")
 
 PIN_SET = [
     pins.test_psi_worked_example,
@@ -56,16 +57,23 @@ MUTANTS = {
 }
 
 
-def _build_mutant(tmp_path, name):
-    find, repl = MUTANTS[name]
-    src = open(SRC).read()
+def build_mutant(tmp_path, name, find, repl, target=SRC):
+    """The oracle library with one replacement in `target` (the other source
+    unchanged)."""
+    src = open(target).read()
     assert src.count(find) == 1, name
     path = tmp_path / ("m_%s.c" % name)
     path.write_text(src.replace(find, repl))
+    others = [f for f in (SRC, SRC_PEN) if f != target]
     so = str(tmp_path / ("m_%s.so" % name))
     subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
-                           "-I", os.path.dirname(SRC), "-o", so, str(path), "-lm"])
+                           "-I", os.path.dirname(SRC), "-o", so, str(path), *others, "-lm"])
     return so
+
+
+def _build_mutant(tmp_path, name):
+    find, repl = MUTANTS[name]
+    return build_mutant(tmp_path, name, find, repl)
 
 
 @pytest.mark.parametrize("name", sorted(MUTANTS))
