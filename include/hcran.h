@@ -304,6 +304,40 @@ int hcran_bf_workspace_size(const hcran_config *cfgs, int32_t n, uint64_t *bytes
 int hcran_bruteforce(const hcran_config *cfgs, int32_t n, const float *gains_dev, void *workspace_dev,
                      void *stream, double *best_ee, int64_t *best_index);
 
+/* ---- penalty form of the selection constraints --------------------------
+ * Sec. IV-A relaxes the binary RRH and subcarrier assignment into C10
+ * (p_{m,k}^{(n)} p_{m',k}^{(n')} <= rho_1, m != m') and C11 (the product of the
+ * powers of any l + 1 users on (m, n) <= rho_2), priced by the multipliers
+ * theta, theta' in eq. (653).  hcran_solve takes the rho -> 0 limit as an
+ * explicit selection; this call solves the penalty form itself, to compare
+ * the two on small instances.  Every (m, k, n) link carries a power; the
+ * iteration is hcran_solve's (Dinkelbach loop around Algorithm 1, same stop
+ * rules) with theta, theta' stepped by
+ *   theta  += delta_v clip((p p' - rho_1)/rho_1, -1, 1) / (ln2 mask_m mask_m'),
+ *   theta' += delta_v clip((prod - rho_2)/rho_2, -1, 1) / (ln2 mask_m^(l+1)),
+ * both projected on >= 0, rho_1 = rho_rel^2 mask_m mask_m',
+ * rho_2 = (rho_rel mask_m)^(l+1); p starts at mask_m / K on every link.  C14
+ * is not enforced.  FP64 arithmetic.
+ *  - cfgs: n instances of one shape, M <= 4, N <= 4, K <= 8, l <= 3,
+ *    N*M*K <= 128, elastic users only (Ks = 0), unit weights; host memory
+ *    read during the call.
+ *  - gains_dev: float32 Gamma[n][m][k], instance b at element
+ *    b * ((N*M*K + 3) / 4 * 4), device memory, 16-byte aligned.
+ *  - tol: tolerances and caps as for hcran_solve (tie_eps unused).
+ *  - rho_rel in (0, 1).
+ *  - workspace_dev: hcran_penalty_workspace_size() bytes, 256-byte aligned,
+ *    owned by the caller; the library allocates no device memory.
+ *  - Enqueues one kernel (one CTA per instance) on `stream`, synchronises it
+ *    and writes to host memory ee[n], and when not NULL p[n*N*M*K] (W, the
+ *    gain array's order), iters[3*n] (Dinkelbach, SCALE, dual), c10_max[n]
+ *    and c11_max[n] (the largest C10 / C11 product over rho_1 / rho_2).
+ *  - HCRAN_EINVAL for a bad or mixed shape or argument, HCRAN_ECUDA on a
+ *    CUDA error. */
+int hcran_penalty_workspace_size(const hcran_config *cfgs, int32_t n, uint64_t *bytes);
+int hcran_penalty_solve(const hcran_config *cfgs, int32_t n, const float *gains_dev, const hcran_tol *tol,
+                        double rho_rel, void *workspace_dev, void *stream, double *ee, double *p,
+                        int32_t *iters, double *c10_max, double *c11_max);
+
 /* ---- allocation-free single-instance solve ----------------------------
  * The paper has no counterpart: this entry point exists for callers that
  * cannot allocate device memory (a process whose device memory belongs to

@@ -14,9 +14,10 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libhcran.so")
-SOURCES = ["hcran_kernel.cu", "hcran_api.cu", "hcran_noalloc.cu", "mlp_kernels.cu", "hcran_bf.cu"]
-# the comparator's FP64 search keeps the operation order it is written in (no FMA contraction)
-EXTRA = {"hcran_bf.cu": ["-fmad=false"]}
+SOURCES = ["hcran_kernel.cu", "hcran_api.cu", "hcran_noalloc.cu", "mlp_kernels.cu", "hcran_bf.cu", "hcran_pen.cu"]
+# the comparator's FP64 search and the penalty form keep the operation order they are written in
+# (no FMA contraction)
+EXTRA = {"hcran_bf.cu": ["-fmad=false"], "hcran_pen.cu": ["-fmad=false"]}
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC"]
 

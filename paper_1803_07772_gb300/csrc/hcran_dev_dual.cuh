@@ -126,9 +126,9 @@ __device__ int dual_loop(const Ctx &c, Shared &sh, float *dyn, const KDims &kd, 
     // the partials of the warps (warp sweeps) or of the teams (team sweeps)
     const int parts = kd.teams > 0 ? kd.teams : kWarps;
     const int wstride = kd.teams > 0 ? team_stride(kd) : warp_stride(kd);
-    const float *wp0 = kd.teams > 0 ? team_buf(dyn, kd, 0).wp : warp_buf(dyn, kd, 0).wp;
-    const float *wr0 = kd.teams > 0 ? team_buf(dyn, kd, 0).wr : warp_buf(dyn, kd, 0).wr;
-    const float *wa0 = kd.teams > 0 ? team_buf(dyn, kd, 0).wa : warp_buf(dyn, kd, 0).wa;
+    const float *wp0 = kd.teams > 0 ? team_buf(kd, 0).wp : warp_buf(dyn, kd, 0).wp;
+    const float *wr0 = kd.teams > 0 ? team_buf(kd, 0).wr : warp_buf(dyn, kd, 0).wr;
+    const float *wa0 = kd.teams > 0 ? team_buf(kd, 0).wa : warp_buf(dyn, kd, 0).wa;
     for (int t = threadIdx.x; t < c.M + c.Ks; t += kThreads) {
       if (t < c.M) {
         const int m = t;

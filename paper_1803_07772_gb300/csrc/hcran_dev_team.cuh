@@ -29,18 +29,23 @@ namespace hcran {
 struct TeamBuf {
   float *p, *pi, *X;               // [Upmax] per slot of the current subcarrier
   int *k;                          // [Upmax]
+  float2 *zw;                      // [Mmax * NPmax] nonzero SIC multipliers, compact, in item order:
+                                   //   (z / Gamma_{m,a}, z / Gamma_{m,b}) of pair (a, b)
+  int2 *zq;                        // [Mmax * NPmax] their slots (a, b)
   float *Pt, *pio, *Sp, *Sm, *wp;  // [Mmax]
   float *zd;                       // [Mmax * NPmax] SIC multipliers of the subcarrier (0: inactive)
-  float *zs;                       // [Mmax * NPmax] the nonzero ones, compact, in item order
-  int *zl;                         // [Mmax * NPmax] their pair items
   float *part;                     // [3 * team threads] per-thread partial sums
   float *wr, *wa;                  // [KSmax] streaming rate / alpha partials of the team
   int *cnt;                        // [4] nonzero multipliers of the subcarrier
   float *stage0, *stage1;          // staging buffers
 };
 
-__device__ __forceinline__ TeamBuf team_buf(float *dyn, const KDims &kd, int team) {
-  float *b = dyn + dyn_head_floats(kd) + (size_t)team * team_stride(kd);
+// Views are built from hcran_dyn itself and passed by value into inlined
+// steps, so that every pointer stays a register holding a shared-memory
+// address: a view passed by reference lives in local memory, and each access
+// through it then waits on a local load first.
+__device__ __forceinline__ TeamBuf team_buf(const KDims &kd, int team) {
+  float *b = hcran_dyn + dyn_head_floats(kd) + team * team_stride(kd);
   const int np = kd.NPmax > 0 ? kd.NPmax : 1;
   TeamBuf t;
   t.stage0 = b;  // staging buffers first: 16-byte aligned
@@ -50,14 +55,14 @@ __device__ __forceinline__ TeamBuf team_buf(float *dyn, const KDims &kd, int tea
   t.pi = b; b += kd.Upmax;
   t.X = b; b += kd.Upmax;
   t.k = reinterpret_cast<int *>(b); b += kd.Upmax;
+  t.zw = reinterpret_cast<float2 *>(b); b += 2 * kd.Mmax * np;  // 8-byte aligned: Upmax is a multiple of 4
+  t.zq = reinterpret_cast<int2 *>(b); b += 2 * kd.Mmax * np;
   t.Pt = b; b += kd.Mmax;
   t.pio = b; b += kd.Mmax;
   t.Sp = b; b += kd.Mmax;
   t.Sm = b; b += kd.Mmax;
   t.wp = b; b += kd.Mmax;
   t.zd = b; b += kd.Mmax * np;
-  t.zs = b; b += kd.Mmax * np;
-  t.zl = reinterpret_cast<int *>(b); b += kd.Mmax * np;
   t.part = b; b += 3 * team_threads(kd);
   t.wr = b; b += (kd.KSmax > 0 ? kd.KSmax : 1);
   t.wa = b; b += (kd.KSmax > 0 ? kd.KSmax : 1);
@@ -73,8 +78,9 @@ __device__ __forceinline__ void team_bar(int team, int nthreads) {
 // Link pass of subcarrier n by one team (tt: thread in the team, TS: team
 // size) at the point in tb.p / tb.k; same quantities as link_subcarrier.
 // Ends with the team's barrier, after which the stage buffer may be refilled.
-__device__ void team_link(const Ctx &c, const Shared &sh, const TeamBuf &tb, const SubView &v,
-                          const float *szeta, int n, bool dual, float delta, int team, int tt, int TS) {
+__device__ __forceinline__ void team_link(const Ctx &c, const Shared &sh, const TeamBuf tb, const SubView v,
+                                          const float *szeta, int n, bool dual, float delta, int team, int tt,
+                                          int TS) {
   const int M = c.M, U = c.U, l = c.l, Up = c.Up;
   const float *sl = v.slab;
   for (int j = tt; j < M; j += TS) {
@@ -139,7 +145,7 @@ __device__ void team_link(const Ctx &c, const Shared &sh, const TeamBuf &tb, con
       tb.zd[it] = both ? (float)zz : 0.f;
     }
     team_bar(team, TS);
-    if (tt < 32) {  // the team's first warp compacts
+    if (tt < 32) {  // the team's first warp compacts, with the weights the row sums need
       int q0 = 0;
       for (int base = 0; base < items; base += 32) {
         const int it = base + tt;
@@ -147,8 +153,9 @@ __device__ void team_link(const Ctx &c, const Shared &sh, const TeamBuf &tb, con
         const unsigned bal = __ballot_sync(0xffffffffu, zf != 0.f);
         if (zf != 0.f) {
           const int q = q0 + __popc(bal & ((1u << tt) - 1u));
-          tb.zl[q] = it;
-          tb.zs[q] = zf;
+          const int ua = sh.item_a[it], ub = sh.item_b[it];
+          tb.zq[q] = make_int2(ua, ub);
+          tb.zw[q] = make_float2(zf * v.ginv[ua], zf * v.ginv[ub]);
         }
         q0 += __popc(bal);
       }
@@ -165,13 +172,13 @@ __device__ void team_link(const Ctx &c, const Shared &sh, const TeamBuf &tb, con
     const int j = h / C, ch = h - j * C;
     const float *row = sl + j * Up;
     float sp = 0.f, sm = 0.f, acc = 0.f;
-    for (int q = ch; q < nnz; q += C) {
-      const int it = tb.zl[q];
-      const int ua = sh.item_a[it], ub = sh.item_b[it];
-      const float cc = row[ua] * v.ginv[ua] - row[ub] * v.ginv[ub];
-      const float z = tb.zs[q];
-      if (cc > 0.f) sp += z * cc;
-      else sm -= z * cc;
+#pragma unroll 2
+    for (int q = ch; q < nnz; q += C) {  // z times the coefficient, whose sign it keeps
+      const int2 ab = tb.zq[q];
+      const float2 wz = tb.zw[q];
+      const float t = row[ab.x] * wz.x - row[ab.y] * wz.y;
+      if (t > 0.f) sp += t;
+      else sm -= t;
     }
     if (dual)
       for (int u = ch; u < U; u += C) acc += row[u] * tb.pi[u];
@@ -219,7 +226,7 @@ __device__ void team_link(const Ctx &c, const Shared &sh, const TeamBuf &tb, con
 
 // Closed-form KKT power of every slot of subcarrier n by one team (as
 // power_subcarrier); the caller synchronises the team afterwards.
-__device__ __forceinline__ float team_power(const Ctx &c, const Shared &sh, const TeamBuf &tb, const SubView &v,
+__device__ __forceinline__ float team_power(const Ctx &c, const Shared &sh, const TeamBuf tb, const SubView v,
                                             const float *szeta, int n, int tt, int TS) {
   float dmax = 0.f;
   for (int u = tt; u < c.U; u += TS) {
@@ -258,7 +265,8 @@ __device__ float team_sweep(const Ctx &c, Shared &sh, float *dyn, const KDims &k
   const int team = team_of(kd, warp);
   if (team >= T) return 0.f;
   const int tt = (int)threadIdx.x - team * TS;
-  const TeamBuf tb = team_buf(dyn, kd, team);
+  const TeamBuf tb = team_buf(kd, team);
+  (void)dyn;
   const double *zsrc = MODE == kFused ? c.zsic_next : c.zsic;
   if (MODE != kLinkOnly) {
     for (int j = tt; j < c.M; j += TS) tb.wp[j] = 0.f;

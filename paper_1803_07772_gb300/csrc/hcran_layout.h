@@ -193,15 +193,15 @@ HCRAN_HD int warp_buf_floats(const KDims &k) {
   return int(al4(warp_work_floats(k))) + (k.staged ? 2 * stage_buf_floats(k) : 0);
 }
 // Team sweeps: a team of kWarps / teams warps works on one subcarrier at a
-// time.  Per team: slot arrays p, pi, X, k [Upmax]; per-RRH totals, price
-// sums, SIC+, SIC-, power partials [Mmax]; the SIC multipliers of the
-// subcarrier densely and as a compact list of the nonzero ones (values and
-// items) [Mmax * NPmax]; three partial sums per thread; the streaming rate and
-// alpha partials [KSmax]; a counter; then the two staging buffers.
+// time.  Per team: the two staging buffers; slot arrays p, pi, X, k [Upmax];
+// a compact list of the nonzero SIC multipliers (two weights, two slots)
+// [Mmax * NPmax]; per-RRH totals, price sums, SIC+, SIC-, power partials
+// [Mmax]; the SIC multipliers of the subcarrier [Mmax * NPmax]; three partial
+// sums per thread; the streaming rate and alpha partials [KSmax]; a counter.
 HCRAN_HD int team_threads(const KDims &k) { return (kWarps / (k.teams > 0 ? k.teams : 1)) * 32; }
 HCRAN_HD int team_work_floats(const KDims &k) {
   const int np = k.NPmax > 0 ? k.NPmax : 1;
-  return int(al4(4 * k.Upmax + 5 * k.Mmax + 3 * k.Mmax * np + 3 * team_threads(k) +
+  return int(al4(4 * k.Upmax + 5 * k.Mmax + 5 * k.Mmax * np + 3 * team_threads(k) +
                  2 * (k.KSmax > 0 ? k.KSmax : 1) + 4));
 }
 HCRAN_HD int team_stride(const KDims &k) { return team_work_floats(k) + 2 * stage_buf_floats(k); }

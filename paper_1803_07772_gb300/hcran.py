@@ -61,7 +61,8 @@ EXPORTS = ["hcran_create", "hcran_workspace_size", "hcran_gain_elems", "hcran_pr
            "hcran_get_phase_cycles", "hcran_last_launch_count", "hcran_destroy",
            "hcran_solve_noalloc", "hcran_get_schedule", "hcran_set_schedule", "hcran_autotune",
            "hcran_solve_graph", "hcran_warm_rows", "hcran_warm_features", "hcran_solve_warm",
-           "hcran_set_state", "hcran_set_wait_limit", "hcran_bf_workspace_size", "hcran_bruteforce"]
+           "hcran_set_state", "hcran_set_wait_limit", "hcran_bf_workspace_size", "hcran_bruteforce",
+           "hcran_penalty_workspace_size", "hcran_penalty_solve"]
 # include/hcran_mlp.h: tensor-core kernels of the warm-start network
 MLP_EXPORTS = ["hcran_mlp_dense", "hcran_mlp_tc_status", "hcran_mlp_create", "hcran_mlp_destroy",
                "hcran_mlp_param_count", "hcran_mlp_get_params", "hcran_mlp_set_params", "hcran_mlp_get_grads",
@@ -104,6 +105,9 @@ def load(build_if_missing: bool = True):
         "hcran_set_wait_limit": ([vp, C.c_int64, C.c_int32], C.c_int),
         "hcran_bf_workspace_size": ([C.POINTER(Config), C.c_int32, C.POINTER(C.c_uint64), _i64p], C.c_int),
         "hcran_bruteforce": ([C.POINTER(Config), C.c_int32, vp, vp, vp, _dp, _i64p], C.c_int),
+        "hcran_penalty_workspace_size": ([C.POINTER(Config), C.c_int32, C.POINTER(C.c_uint64)], C.c_int),
+        "hcran_penalty_solve": ([C.POINTER(Config), C.c_int32, vp, C.POINTER(Tol), C.c_double, vp, vp, _dp, _dp,
+                                 _ip, _dp, _dp], C.c_int),
         "hcran_mlp_dense": ([vp, vp, vp, vp, C.c_int64, C.c_int32, C.c_int32, C.c_int32, vp, vp], C.c_int),
         "hcran_mlp_tc_status": ([_ip], C.c_int),
         "hcran_mlp_create": ([C.POINTER(vp), C.c_uint64, C.c_int64], C.c_int),
@@ -366,6 +370,39 @@ def bruteforce(instances, gains, stream=None):
                                                     C.c_void_p(ws.data_ptr()), C.c_void_p(st.cuda_stream),
                                                     ee.ctypes.data_as(_dp), idx.ctypes.data_as(_i64p)))
     return ee, idx, na.value
+
+
+def penalty_solve(instances, gains, tol: Tol, rho_rel: float = 1e-3, stream=None) -> dict:
+    """Penalty form of C10 / C11 on the GPU (include/hcran.h): instances of
+    one shape, elastic users only; gains a CUDA float32 tensor packed as
+    hcran_inputs.pack_batch packs them.  Returns host arrays ee [n],
+    p [n][N][M][K], iters [n][3], c10_max [n], c11_max [n]."""
+    import torch
+    lib = load()
+    n = len(instances)
+    cfgs = (Config * n)()
+    keep = []
+
+    def d(x):
+        a = np.ascontiguousarray(x, dtype=np.float64)
+        keep.append(a)
+        return a.ctypes.data_as(_dp)
+    for i, inst in enumerate(instances):
+        cfgs[i] = Config(inst.M, inst.N, inst.K, inst.Ks, inst.l, d(inst.pmax), d(inst.eta), d(inst.Pc),
+                         d(inst.Pf), float(inst.Bn_hz), float(inst.N0_w_per_hz), None, None,
+                         float(inst.zbar_bits), d(inst.w) if inst.w is not None else None)
+    nb = C.c_uint64()
+    _check("hcran_penalty_workspace_size", lib.hcran_penalty_workspace_size(cfgs, n, C.byref(nb)))
+    ws = torch.empty(max(nb.value, 256), dtype=torch.uint8, device=gains.device)
+    st = stream if stream is not None else torch.cuda.current_stream(gains.device)
+    i0 = instances[0]
+    out = dict(ee=np.zeros(n), p=np.zeros((n, i0.N, i0.M, i0.K)), iters=np.zeros((n, 3), np.int32),
+               c10_max=np.zeros(n), c11_max=np.zeros(n))
+    _check("hcran_penalty_solve", lib.hcran_penalty_solve(
+        cfgs, n, C.c_void_p(gains.data_ptr()), C.byref(tol), float(rho_rel), C.c_void_p(ws.data_ptr()),
+        C.c_void_p(st.cuda_stream), out["ee"].ctypes.data_as(_dp), out["p"].ctypes.data_as(_dp),
+        out["iters"].ctypes.data_as(_ip), out["c10_max"].ctypes.data_as(_dp), out["c11_max"].ctypes.data_as(_dp)))
+    return out
 
 
 def solve_noalloc(inst, gains, tol: Tol, stream=None) -> dict:
