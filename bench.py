@@ -364,6 +364,14 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+def _hbm_peak() -> float:
+    """Measured copy bandwidth of the GB300s (GB/s), else the fallback."""
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
+    except Exception:
+        return 6800.0
+
+
 def large_leg(dev, count=256):
     """The large workload (1 HPN + 32 LPNs, 1024 subcarriers, 512 users, l = 4;
     about 69 MB of FP32 gains per instance, 17.7 GB for 256): every instance
@@ -383,6 +391,8 @@ def large_leg(dev, count=256):
         g = torch.from_numpy(gains).to(dev)
     del gains
     tol = make_tol(WORKLOADS[name]["tol"])
+    teams_planned = s.stream_teams()
+    s.autotune(g, tol)  # the team count of the streamed sweeps
     s.solve(g, tol)
     stream.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -396,6 +406,8 @@ def large_leg(dev, count=256):
     ab = algorithmic_bytes(insts, summ["iters"], links)
     out = {"workload": name, "instances": count, "instances_per_s": count / sec, "seconds": sec,
            "algorithmic_gbs": ab / sec / 1e9, "schedule": "one CTA per instance, streamed",
+           "algorithmic_frac_of_measured_hbm": ab / sec / 1e9 / _hbm_peak(),
+           "teams": {"planned": int(teams_planned), "autotuned": int(s.stream_teams())},
            "gain_bytes": int(4 * sum(i.cost for i in insts)),
            "mean_iters": np.mean(summ["iters"], axis=0).tolist(),
            "status_counts": {str(k): int(v) for k, v in zip(*np.unique(summ["status"], return_counts=True))},
@@ -602,7 +614,8 @@ def run_profile_case():
 # device code of the solve kernel (the host planner and ABI files are left out:
 # they do not change what one launch reads and writes)
 KERNEL_FILES = ("hcran_kernel.cu", "hcran_layout.h", "hcran_dev_common.cuh", "hcran_dev_link.cuh",
-                "hcran_dev_dual.cuh", "hcran_dev_resident.cuh", "hcran_dev_select.cuh")
+                "hcran_dev_dual.cuh", "hcran_dev_team.cuh", "hcran_dev_resident.cuh", "hcran_dev_select.cuh",
+                "hcran_dev_warm.cuh")
 
 
 def run_profile_large():

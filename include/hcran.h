@@ -228,12 +228,21 @@ int hcran_set_schedule(hcran_t h, const int32_t *cluster_size);
  * exactly max(max_dual_probe / 4, 1) and that plus max_dual_probe dual
  * iterations, and keeps the schedule whose extra max_dual_probe dual
  * iterations take less time (the dual loop is almost all of a full solve).
+ * When the streamed class runs team sweeps, it times the same probe on the
+ * class's first wave (at most one instance per SM) for every team count from
+ * 1 to the planner's (all of whose buffers fit) and keeps the fastest, as if
+ * set by hcran_set_schedule's -T.
  * Probes overwrite the solution state in the workspace (a later solve starts
  * afresh).  Synchronises the stream.  gains_dev and workspace as for
  * hcran_solve; tol supplies tie_eps and q_init.  Returns HCRAN_EINVAL on bad
  * arguments, HCRAN_ECUDA on a CUDA error. */
 int hcran_autotune(hcran_t h, const float *gains_dev, const hcran_tol *tol, void *workspace_dev, void *stream,
                    int32_t max_dual_probe);
+
+/* Teams of warps the streamed class's sweeps run (0 when the class is empty
+ * or its warps stage their own subcarriers); see hcran_set_schedule and
+ * hcran_autotune.  Host only.  HCRAN_EINVAL on a NULL argument. */
+int hcran_get_stream_teams(hcran_t h, int32_t *teams);
 
 /* hcran_solve through a CUDA graph: the launch sequence (one persistent
  * launch per cluster size) is captured on the first call for a given

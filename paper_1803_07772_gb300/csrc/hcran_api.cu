@@ -761,13 +761,51 @@ extern "C" int hcran_autotune(hcran_t h, const float *gains_dev, const hcran_tol
         if (h->descs[b].N >= C2) cls[b] = class_of(C2);
       }
   }
+  // the streamed class: how many teams its sweeps run (the planner takes as
+  // many as fit; fewer, larger teams give each subcarrier more threads)
+  int32_t teams = h->stream_teams;
+  {
+    const LaunchClass L = h->classes[kNumClasses - 1];
+    if (rc == HCRAN_OK && L.count > 0 && L.kd.staged && L.kd.teams > 0) {
+      const int S = std::min(L.count, sms);  // the first wave of the class
+      float best = 0.f;
+      int best_t = 0;
+      for (int t = 1; t <= L.kd.teams && rc == HCRAN_OK; t++) {
+        KDims kd = L.kd;
+        kd.teams = t;
+        if (dyn_smem_bytes(kd) > kMaxDynSmem) continue;
+        float ms[2] = {0.f, 0.f};
+        for (int j = 0; j < 2 && rc == HCRAN_OK; j++) {
+          int l = 0;
+          if (cudaEventRecord(e0, st) != cudaSuccess ||
+              launch_class(h, L, kd, 1, S, kNumClasses - 1, gains_dev, j ? t2 : t1, ws, st, &l) != cudaSuccess ||
+              cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+              cudaEventElapsedTime(&ms[j], e0, e1) != cudaSuccess)
+            rc = HCRAN_ECUDA;
+        }
+        if (rc == HCRAN_OK && (best_t == 0 || ms[1] - ms[0] < best)) {
+          best = ms[1] - ms[0];
+          best_t = t;
+        }
+      }
+      if (rc == HCRAN_OK && best_t > 0) teams = best_t;
+    }
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (rc != HCRAN_OK) return rc;
-  if (cls != h->cls) {
+  if (cls != h->cls || teams != h->stream_teams) {
     h->cls = cls;
+    h->stream_teams = teams;
     if (build_classes(h) != 0) return HCRAN_EINVAL;
   }
+  return HCRAN_OK;
+}
+
+extern "C" int hcran_get_stream_teams(hcran_t h, int32_t *teams) {
+  if (!h || !teams) return HCRAN_EINVAL;
+  const LaunchClass &L = h->classes[kNumClasses - 1];
+  *teams = L.count > 0 ? L.kd.teams : 0;
   return HCRAN_OK;
 }
 

@@ -62,7 +62,7 @@ EXPORTS = ["hcran_create", "hcran_workspace_size", "hcran_gain_elems", "hcran_pr
            "hcran_solve_noalloc", "hcran_get_schedule", "hcran_set_schedule", "hcran_autotune",
            "hcran_solve_graph", "hcran_warm_rows", "hcran_warm_features", "hcran_solve_warm",
            "hcran_set_state", "hcran_set_wait_limit", "hcran_bf_workspace_size", "hcran_bruteforce",
-           "hcran_penalty_workspace_size", "hcran_penalty_solve"]
+           "hcran_penalty_workspace_size", "hcran_penalty_solve", "hcran_get_stream_teams"]
 # include/hcran_mlp.h: tensor-core kernels of the warm-start network
 MLP_EXPORTS = ["hcran_mlp_dense", "hcran_mlp_tc_status", "hcran_mlp_create", "hcran_mlp_destroy",
                "hcran_mlp_param_count", "hcran_mlp_get_params", "hcran_mlp_set_params", "hcran_mlp_get_grads",
@@ -106,6 +106,7 @@ def load(build_if_missing: bool = True):
         "hcran_bf_workspace_size": ([C.POINTER(Config), C.c_int32, C.POINTER(C.c_uint64), _i64p], C.c_int),
         "hcran_bruteforce": ([C.POINTER(Config), C.c_int32, vp, vp, vp, _dp, _i64p], C.c_int),
         "hcran_penalty_workspace_size": ([C.POINTER(Config), C.c_int32, C.POINTER(C.c_uint64)], C.c_int),
+        "hcran_get_stream_teams": ([vp, _ip], C.c_int),
         "hcran_penalty_solve": ([C.POINTER(Config), C.c_int32, vp, C.POINTER(Tol), C.c_double, vp, vp, _dp, _dp,
                                  _ip, _dp, _dp], C.c_int),
         "hcran_mlp_dense": ([vp, vp, vp, vp, C.c_int64, C.c_int32, C.c_int32, C.c_int32, vp, vp], C.c_int),
@@ -216,6 +217,12 @@ class Solver:
             self.h, C.c_void_p(gains.data_ptr()), C.byref(tol), C.c_void_p(self.workspace.data_ptr()),
             C.c_void_p(self.stream.cuda_stream), int(max_dual_probe)))
         return self.schedule()
+
+    def stream_teams(self) -> int:
+        """Teams of warps the streamed class's sweeps run (0: none)."""
+        v = C.c_int32()
+        _check("hcran_get_stream_teams", self.lib.hcran_get_stream_teams(self.h, C.byref(v)))
+        return v.value
 
     def warm_rows(self) -> int:
         n = C.c_int64()

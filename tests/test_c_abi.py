@@ -43,6 +43,7 @@ static int null_calls(void) {
   bad += hcran_bf_workspace_size(NULL, 0, NULL, NULL) != HCRAN_EINVAL;
   bad += hcran_bruteforce(NULL, 0, NULL, NULL, NULL, NULL, NULL) != HCRAN_EINVAL;
   bad += hcran_penalty_workspace_size(NULL, 0, NULL) != HCRAN_EINVAL;
+  bad += hcran_get_stream_teams(NULL, NULL) != HCRAN_EINVAL;
   bad += hcran_penalty_solve(NULL, 0, NULL, NULL, 0.0, NULL, NULL, NULL, NULL, NULL, NULL, NULL) != HCRAN_EINVAL;
   hcran_destroy(NULL);
   bad += hcran_mlp_dense(NULL, NULL, NULL, NULL, 0, 16, 16, 0, NULL, NULL) != HCRAN_MLP_EINVAL;

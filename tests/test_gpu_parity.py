@@ -230,6 +230,29 @@ def test_team_sweeps_match_oracle_at_fixed_counts():
             compare(inst, r, o, "%d teams" % teams)
 
 
+def test_autotune_picks_a_team_count_for_the_streamed_class():
+    """Instances on the streamed schedule with team sweeps: the autotuner
+    times every team count that fits and keeps one; the solve then still
+    matches the oracle at fixed counts."""
+    from paper_1803_07772_gb300 import make_tol
+    insts = _batch_subset(count=3)
+    tol = Tolerances(tol_dinkelbach=0.0, tol_scale=0.0, tol_dual=0.0,
+                     max_dinkelbach=2, max_scale=3, max_dual=40)
+    s, g = _solver(insts)
+    s.set_schedule(np.full(len(insts), -4, np.int32))
+    assert s.stream_teams() == 4
+    s.autotune(g, make_tol(tol, tie_eps=TIE_BAND), max_dual_probe=20)
+    t = s.stream_teams()
+    print("team count after autotune", t)
+    assert 1 <= t <= 4
+    s.solve(g, make_tol(tol, tie_eps=TIE_BAND))
+    for i, inst in enumerate(insts):
+        r = s.get(i)
+        o = oracle.solve(inst, tol)
+        assert r["iters"] == o.iters
+        compare(inst, r, o, "%d teams (autotuned)" % t)
+
+
 def test_autotuned_schedule_is_valid_and_matches_oracle():
     from paper_1803_07772_gb300 import make_tol
     insts = _batch_subset(count=4)
