@@ -62,7 +62,10 @@ struct Shared {
   double redd[kWarps];
   float redf[kWarps];
   int redi[kWarps];
-  unsigned long long bar[kWarps][2];  // per-warp mbarriers of the two staging buffers
+  unsigned long long bar[kWarps][2];   // per-warp (or per-team) mbarriers of the two staging buffers: filled
+  unsigned long long ebar[kWarps][2];  // per-team mbarriers of the two staging buffers: released (team sweeps
+                                       // with a producer warp)
+  unsigned eph;                        // parity of the next phase of each ebar the producer waits for
   long long cyc[8];  // SM clock cycles per phase of the current instance (thread 0)
   double cxd;        // cluster reductions: this CTA's value, read by the peers
   float cxf;

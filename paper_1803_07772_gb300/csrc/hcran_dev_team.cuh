@@ -4,9 +4,10 @@
 // 33 x 1024 x 512 shape: 28 MB per instance), every dual iteration streams
 // the state of each subcarrier from HBM.  The CTA's warps form kd.teams teams
 // of kWarps / kd.teams warps; team t works on subcarriers n0 + t, n0 + t +
-// teams, ... one at a time, while its first thread prefetches the next one
-// into the team's other staging buffer with one-dimensional bulk copies
-// (cp.async.bulk) completed on the team's mbarrier.  The steps of one
+// teams, ... one at a time, while the next one is prefetched into the team's
+// other staging buffer with one-dimensional bulk copies (cp.async.bulk)
+// completed on the team's mbarrier: issued by a producer warp when the teams
+// leave one over, else by the team's first thread.  The steps of one
 // subcarrier are those of the warp sweep (hcran_dev_link.cuh), shared out
 // over the team's threads and separated by the team's named barrier:
 //   power     closed-form KKT power per slot (fused sweeps)
@@ -252,8 +253,44 @@ __device__ __forceinline__ float team_power(const Ctx &c, const Shared &sh, cons
   return dmax;
 }
 
+__device__ __forceinline__ void mbar_arrive_cta(unsigned long long *bar) {
+  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}" ::"r"(smem_addr(bar))
+               : "memory");
+}
+
+// Producer of the team sweeps when kd.teams leaves a warp over (3 teams of 5
+// warps): the first lane of the last warp issues every team's staging copies,
+// in the order the teams consume them, so that no team's thread spends its
+// time issuing them.  Team t's i-th subcarrier goes to its buffer i & 1; from
+// the third on, the producer first waits until the team has released the
+// buffer (its first thread arrives on ebar after the subcarrier's last
+// barrier).  sh.eph keeps the parity of the next release phase of every
+// buffer across sweeps: each use of a buffer completes one phase.
+__device__ void team_produce(const Ctx &c, Shared &sh, const KDims &kd, const double *zsrc) {
+  const int T = kd.teams;
+  unsigned ph = sh.eph;
+  const int rounds = (c.n1 - c.n0 + T - 1) / T;
+  for (int i = 0; i < rounds; i++)
+    for (int t = 0; t < T; t++) {
+      const int n = c.n0 + t + i * T;
+      if (n >= c.n1) continue;
+      const int b = i & 1, bit = 2 * t + b;
+      if (i >= 2) {
+        if (!mbar_wait(&sh.ebar[t][b], (ph >> bit) & 1u, sh.spin_limit)) sh.abort = 1;
+        ph ^= 1u << bit;
+      }
+      const TeamBuf tb = team_buf(kd, t);
+      issue_stage(c, sh, kd, b ? tb.stage1 : tb.stage0, t, b, n, zsrc);
+    }
+  // the last use of each buffer completes a phase nobody waits for this sweep
+  for (int t = 0; t < T; t++)
+    for (int b = 0; b < 2; b++)
+      if (c.n0 + t + b * T < c.n1) ph ^= 1u << (2 * t + b);
+  sh.eph = ph;
+}
+
 // team of warp `warp` (kd.teams teams of kWarps / kd.teams warps; warps past
-// the last team take no part in the sweeps)
+// the last team take no part in the sweeps, except the producer)
 __device__ __forceinline__ int team_of(const KDims &kd, int warp) { return warp / (kWarps / kd.teams); }
 
 // One sweep of every team over its subcarriers (same contract as sweep).
@@ -263,7 +300,12 @@ __device__ float team_sweep(const Ctx &c, Shared &sh, float *dyn, const KDims &k
   const int warp = threadIdx.x >> 5;
   const int T = kd.teams, TS = team_threads(kd);
   const int team = team_of(kd, warp);
-  if (team >= T) return 0.f;
+  const bool producer = (kWarps % T) != 0;  // a warp is left over: it issues the copies
+  if (team >= T) {
+    if (producer && warp == kWarps - 1 && (threadIdx.x & 31) == 0)
+      team_produce(c, sh, kd, MODE == kFused ? c.zsic_next : c.zsic);
+    return 0.f;
+  }
   const int tt = (int)threadIdx.x - team * TS;
   const TeamBuf tb = team_buf(kd, team);
   (void)dyn;
@@ -279,14 +321,14 @@ __device__ float team_sweep(const Ctx &c, Shared &sh, float *dyn, const KDims &k
   float dl = 0.f;
   int i = 0;
   if (c.n0 + team < c.n1) {
-    if (tt == 0) issue_stage(c, sh, kd, tb.stage0, team, 0, c.n0 + team, zsrc);
+    if (!producer && tt == 0) issue_stage(c, sh, kd, tb.stage0, team, 0, c.n0 + team, zsrc);
     pending |= 1u;
   }
   for (int n = c.n0 + team; n < c.n1; n += T, i++) {
     const int b = i & 1;
     const int nn = n + T;
     if (nn < c.n1) {  // buffer b^1 was released by the barrier that ended the last subcarrier
-      if (tt == 0) issue_stage(c, sh, kd, b ? tb.stage0 : tb.stage1, team, b ^ 1, nn, zsrc);
+      if (!producer && tt == 0) issue_stage(c, sh, kd, b ? tb.stage0 : tb.stage1, team, b ^ 1, nn, zsrc);
       pending |= 2u >> b;
     }
     const bool ok = mbar_wait(&sh.bar[team][b], (phase >> b) & 1u, sh.spin_limit);
@@ -305,6 +347,7 @@ __device__ float team_sweep(const Ctx &c, Shared &sh, float *dyn, const KDims &k
     }
     team_bar(team, TS);
     team_link(c, sh, tb, v, szeta, n, MODE != kLinkOnly, delta, team, tt, TS);
+    if (producer && tt == 0) mbar_arrive_cta(&sh.ebar[team][b]);  // buffer b is free again
   }
   return warp_max(dl);
 }

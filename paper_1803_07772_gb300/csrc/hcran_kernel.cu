@@ -321,8 +321,11 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (lane == 0) {
     mbar_init(&sh.bar[warp][0], 1);
     mbar_init(&sh.bar[warp][1], 1);
+    mbar_init(&sh.ebar[warp][0], 1);
+    mbar_init(&sh.ebar[warp][1], 1);
   }
   if (threadIdx.x == 0) {
+    sh.eph = 0u;
     mbar_init(&sh.stall_bar, 1);
     sh.spin_limit = tol.spin_limit > 0 ? tol.spin_limit : (long long)kSpinLimit;
   }
