@@ -189,6 +189,37 @@ def test_set_schedule_validates_and_applies():
     lib.hcran_destroy(h)
 
 
+def test_streamed_team_count_is_planned_and_set_on_the_host():
+    """The 33 x 1024 x 512 shape stages its subcarriers in teams: the planner
+    takes the most teams whose double buffers fit shared memory (3 of 5
+    warps); hcran_set_schedule's -T forces T teams, all negative entries must
+    agree, and T outside 1 .. 4 is rejected with the plan unchanged."""
+    lib = hcran.load()
+    insts = make_workload("batch-4096-uneven", count=2) + make_workload("large-33x1024x512", count=1)
+    made = [_cfg(i) for i in insts]
+    arr = (hcran.Config * len(made))(*[m[0] for m in made])
+    h = C.c_void_p()
+    assert lib.hcran_create(C.byref(h), arr, len(made), None) == 0
+    teams = C.c_int32()
+
+    def get_teams():
+        assert lib.hcran_get_stream_teams(h, C.byref(teams)) == 0
+        return teams.value
+    assert get_teams() == 3
+    sched = np.zeros(3, np.int32)
+    assert lib.hcran_get_schedule(h, sched.ctypes.data_as(hcran._ip)) == 0
+    for want in (1, 2, 3):
+        s = np.ascontiguousarray(np.where(np.arange(3) == 2, -want, sched), dtype=np.int32)
+        assert lib.hcran_set_schedule(h, s.ctypes.data_as(hcran._ip)) == 0
+        assert get_teams() == want
+    for bad in ([sched[0], sched[1], -5], [-1, sched[1], -2], [sched[0], sched[1], -4]):
+        b = np.ascontiguousarray(bad, dtype=np.int32)  # -4: four teams' buffers exceed shared memory
+        assert lib.hcran_set_schedule(h, b.ctypes.data_as(hcran._ip)) == 1
+        assert get_teams() == 3
+    assert lib.hcran_get_stream_teams(h, None) == 1
+    lib.hcran_destroy(h)
+
+
 def test_kernel_hash_ignores_comments_but_not_code():
     """The hash that ties the stored DRAM-traffic ratio to the device code:
     comment and whitespace edits keep it, a code edit changes it."""
