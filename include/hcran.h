@@ -227,7 +227,8 @@ int hcran_set_schedule(hcran_t h, const int32_t *cluster_size);
  * current schedule), with one Dinkelbach iteration, one SCALE pass and
  * exactly max(max_dual_probe / 4, 1) and that plus max_dual_probe dual
  * iterations, and keeps the schedule whose extra max_dual_probe dual
- * iterations take less time (the dual loop is almost all of a full solve).
+ * iterations take less time (the dual loop is almost all of a full solve);
+ * every probe is timed twice and the shorter time kept.
  * When the streamed class runs team sweeps, it times the same probe on the
  * class's first wave (at most one instance per SM) for every team count from
  * 1 to the planner's (all of whose buffers fit) and keeps the fastest, as if
