@@ -220,6 +220,40 @@ def test_streamed_team_count_is_planned_and_set_on_the_host():
     lib.hcran_destroy(h)
 
 
+def test_penalty_form_validates_shapes_on_the_host():
+    """hcran_penalty_workspace_size / hcran_penalty_solve take one shape of at
+    most 4 RRHs, 4 subcarriers, 8 users, l <= 3 and 128 links, elastic users
+    only, and reject the rest before any device work."""
+    from hcran_inputs import make_instance
+    lib = hcran.load()
+    nb = C.c_uint64()
+
+    def size(insts):
+        made = [_cfg(i) for i in insts]
+        arr = (hcran.Config * len(made))(*[m[0] for m in made])
+        return lib.hcran_penalty_workspace_size(arr, len(made), C.byref(nb))
+    ok = [make_instance(1 + i, M=3, N=2, K=3, Ks=0, l=2) for i in range(2)]
+    assert size(ok) == 0 and nb.value > 0
+    assert size([make_instance(5, M=4, N=4, K=8, Ks=0, l=3)]) == 0   # 128 links
+    for bad in ([make_instance(5, M=5, N=2, K=3, Ks=0, l=2)],       # too many RRHs
+                [make_instance(5, M=3, N=2, K=9, Ks=0, l=2)],       # too many users
+                [make_instance(5, M=3, N=2, K=4, Ks=1, l=2)],       # a streaming user
+                [make_instance(5, M=3, N=2, K=3, Ks=0, l=4)],       # l above 3
+                [ok[0], make_instance(7, M=3, N=3, K=3, Ks=0, l=2)]):  # mixed shapes
+        assert size(bad) == 1
+    made = [_cfg(i) for i in ok]
+    arr = (hcran.Config * 2)(*[m[0] for m in made])
+    tol = hcran.make_tol()
+    ee = np.zeros(2)
+    fake = C.c_void_p(1 << 20)  # aligned, never dereferenced: the call fails before device work
+    args = lambda rho, g=fake, w=fake: lib.hcran_penalty_solve(arr, 2, g, C.byref(tol), rho, w, None,
+                                                                ee.ctypes.data_as(hcran._dp), None, None,
+                                                                None, None)
+    assert args(0.0) == 1 and args(1.0) == 1                # rho_rel outside (0, 1)
+    assert args(1e-3, g=C.c_void_p((1 << 20) + 4)) == 1     # gains not 16-byte aligned
+    assert args(1e-3, w=C.c_void_p((1 << 20) + 16)) == 1    # workspace not 256-byte aligned
+
+
 def test_kernel_hash_ignores_comments_but_not_code():
     """The hash that ties the stored DRAM-traffic ratio to the device code:
     comment and whitespace edits keep it, a code edit changes it."""
