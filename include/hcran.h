@@ -223,7 +223,7 @@ int hcran_set_schedule(hcran_t h, const int32_t *cluster_size);
 
 /* Autotuner of the schedule.  For each cluster size C < 8 in use it times
  * that class's launch against clusters of min(2 C, 8) CTAs on the class's first
- * S instances in launch order (S = the class size, at most two waves of the
+ * S instances in launch order (S = the class size, at most eight waves of the
  * current schedule), with one Dinkelbach iteration, one SCALE pass and
  * exactly max(max_dual_probe / 4, 1) and that plus max_dual_probe dual
  * iterations, and keeps the schedule whose extra max_dual_probe dual

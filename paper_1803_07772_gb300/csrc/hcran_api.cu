@@ -724,10 +724,11 @@ extern "C" int hcran_autotune(hcran_t h, const float *gains_dev, const hcran_tol
     const LaunchClass L = h->classes[k];
     if (L.count == 0) continue;
     const int C = L.csize, C2 = 2 * C < kMaxCluster ? 2 * C : kMaxCluster;
-    // probe: the first S instances of the class in launch order; every one
-    // of them must have a subcarrier for each CTA of the larger cluster
+    // probe: the instances of the class in launch order (at most eight waves
+    // of the current schedule); every one of them must have a subcarrier for
+    // each CTA of the larger cluster
     std::vector<int32_t> probe;
-    const int S = std::min(L.count, 2 * (sms / C));
+    const int S = std::min(L.count, 8 * (sms / C));
     for (int i = 0; i < S; i++) probe.push_back(h->order[L.first + i]);
     bool fits = true;
     for (int32_t b : probe) fits = fits && h->descs[b].N >= C2;
