@@ -637,6 +637,24 @@ def run_profile_large():
                       "fused_sweep_cycles_per_dual_iteration": float(cyc[:, 3].sum() / max(1, s.summary()["iters"][:, 2].sum()))}))
 
 
+def run_profile_penalty():
+    """The penalty form of C10 / C11 on the 256 instances of the optimum
+    workload (one launch, one CTA per instance): the case for ncu."""
+    import torch
+    from hcran_inputs import WORKLOADS, make_workload, pack_batch
+    from paper_1803_07772_gb300 import make_tol
+    from paper_1803_07772_gb300.hcran import penalty_solve
+    name = "optimum-3x2x3"
+    insts = make_workload(name)
+    gains, _ = pack_batch(insts)
+    g = torch.from_numpy(gains).cuda()
+    t0 = time.perf_counter()
+    out = penalty_solve(insts, g, make_tol(WORKLOADS[name]["tol"]))
+    sec = time.perf_counter() - t0
+    print(json.dumps({"profile_penalty": name, "instances": len(insts), "seconds": sec,
+                      "mean_iters": out["iters"].mean(axis=0).tolist(), "mean_ee": float(out["ee"].mean())}))
+
+
 def run_profile_mlp():
     """One forward, loss gradient, backward and Adam step of the warm-start
     network on 2^20 synthetic rows (the profiling case of its kernels)."""
@@ -722,6 +740,8 @@ def main():
                     help="also solve the 256 instances of the 33 x 1024 x 512 workload (about 17.7 GB of gains)")
     ap.add_argument("--warm-train", type=int, default=512, help="training instances of the warm start")
     ap.add_argument("--warm-epochs", type=int, default=8)
+    ap.add_argument("--profile-penalty", action="store_true",
+                    help="the penalty form of C10/C11 on the 256 optimum-workload instances (the case for ncu)")
     ap.add_argument("--profile-large", action="store_true",
                     help="16 instances of the 33 x 1024 x 512 workload with short caps (the small case for ncu)")
     ap.add_argument("--profile-case", action="store_true",
@@ -733,6 +753,9 @@ def main():
         return
     if args.profile_large:
         run_profile_large()
+        return
+    if args.profile_penalty:
+        run_profile_penalty()
         return
     if args.profile_mlp:
         run_profile_mlp()
